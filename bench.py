@@ -1,0 +1,444 @@
+#!/usr/bin/env python3
+"""Benchmark of the UMI detrend path on GB300.
+
+Default workload: 1,000 TESS-like 2-min curves x 18,000 samples (W = 361,
+alpha 2, c 5, 5 iterations), flux resident in HBM, one batched call per step
+(the persistent work-queue kernel, replayed from the CUDA-graph cache).
+
+Prints ONE JSON line (rank 0) with: value = window evaluations per second
+(positions whose trend is produced), curves/s, the live roofline of the
+kernel (ALU-issue bound), the end-to-end number through the host-buffer
+entry point, the one-launch-per-curve form, a short serving run (p50/p99),
+the FP64 oracle on the host cores as a CPU baseline, and SM clocks sampled
+during the timed region.
+
+--impl reference runs the FP64 CPU oracle instead (a bounded sample of the
+same workload per step, on the host cores) and prints the same kind of line.
+Under torchrun each rank detrends its own batch (weak scaling, no collective
+on the data path); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Lane-ops per valid window sample for one window evaluation: 5 iterations x
+# 9 (residual, scale, two sign selects, fma, clamp, square, two sums) + 5 for
+# the upper-RMS scale + 4 for one exact selection pass.
+OPS_PER_SAMPLE = 54
+LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="umi", choices=["umi", "reference"])
+    ap.add_argument("--curves", type=int, default=1000)
+    ap.add_argument("--n", type=int, default=18000)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the per-curve, serving, e2e and CPU-baseline legs")
+    ap.add_argument("--serve-requests", type=int, default=3000)
+    ap.add_argument("--serve-rate", type=float, default=5000.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(dist, value, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def shard_seed(rank):
+    """Each rank detrends its own batch: seeds differ per rank."""
+    from paper_2604_06602_gb300 import synth
+    return synth.BASE_SEED + 1 + 1000 * rank
+
+
+def window_work(flux, offsets, W, min_valid=None):
+    """(produced positions, sum of valid samples over their windows)."""
+    evals, samples = 0, 0
+    for b in range(offsets.size - 1):
+        x = flux[offsets[b]:offsets[b + 1]]
+        w = int(W[b])
+        h = (w - 1) // 2
+        fin = np.isfinite(x)
+        cs = np.concatenate([[0], np.cumsum(fin, dtype=np.int64)])
+        n = x.size
+        j = np.arange(n)
+        lo = np.maximum(0, j - h)
+        hi = np.minimum(n, j + h + 1)
+        nv = cs[hi] - cs[lo]
+        mv = w // 3 if min_valid is None or min_valid < 0 else min_valid
+        prod = fin & (nv >= max(1, mv))
+        evals += int(prod.sum())
+        samples += int(nv[prod].sum())
+    return evals, samples
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": float(max(power))}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_baseline(batch, W, budget_s=12.0):
+    """FP64 oracle on the host cores over a bounded sample of the workload."""
+    import oracle
+    threads = os.cpu_count() or 1
+    k = max(threads, 8)
+    while True:
+        idx = np.arange(min(k, batch.B))
+        sub = batch.subset(idx)
+        t0 = time.perf_counter()
+        oracle.detrend_batch(sub.flux, sub.offsets, W[idx], nthreads=threads)
+        dt = time.perf_counter() - t0
+        if dt * threads >= budget_s or k >= batch.B:
+            break
+        k = min(batch.B, int(k * max(2.0, budget_s / max(dt * threads, 1e-3))))
+    evals, _ = window_work(sub.flux, sub.offsets, W[idx])
+    return {"value": evals / dt, "unit": "window-evals/s", "cores": threads, "kind": "oracle",
+            "sample": "%d of the %d curves (FP64 C oracle, %d pthreads, %.1f s wall)"
+                      % (idx.size, batch.B, threads, dt),
+            "curves_per_s": idx.size / dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2604_06602_gb300 import synth
+    batch = synth.config2(seed=shard_seed(0), n_curves=args.curves, n=args.n)
+    W = np.full(batch.B, oracle.window_length(batch.cadence[0]), np.int32)
+    threads = os.cpu_count() or 1
+    per_step = max(threads, 16)
+    idx_all = np.arange(batch.B)
+    t_steps = []
+    evals = 0
+    for s in range(args.warmup + args.steps):
+        idx = idx_all[(s * per_step) % batch.B:][:per_step]
+        sub = batch.subset(idx)
+        t0 = time.perf_counter()
+        oracle.detrend_batch(sub.flux, sub.offsets, W[idx], nthreads=threads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            t_steps.append(dt)
+            evals += window_work(sub.flux, sub.offsets, W[idx])[0]
+    total = sum(t_steps)
+    value = evals / total
+    line = {
+        "impl": "reference", "metric": "window-evals/s", "value": value, "unit": "window-evals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%d TESS-like curves x %d samples, W=361 (oracle: %d curves per step)"
+                               % (batch.B, args.n, per_step), "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "window-evals/s", "cores": threads, "kind": "oracle",
+                         "sample": "%d curves per step, FP64 C oracle" % per_step},
+        "e2e": {"value": value, "unit": "window-evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_umi(args):
+    import torch
+
+    rank, world, local = dist_env()
+    dist = init_dist(world, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2604_06602_gb300 import build as libbuild
+    from paper_2604_06602_gb300 import synth, umi
+    if rank == 0 or not libbuild.up_to_date():
+        if rank == 0:
+            libbuild.build()
+    barrier(dist)
+    umi.load()
+
+    batch = synth.config2(seed=shard_seed(rank), n_curves=args.curves, n=args.n)
+    W = np.array([umi.window_length(c) for c in batch.cadence], np.int32)
+    evals, samples = window_work(batch.flux, batch.offsets, W)
+    flux = torch.from_numpy(batch.flux).to(dev)
+    trend = torch.empty_like(flux)
+    detr = torch.empty_like(flux)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    umi.set_graph_cache(True)
+
+    for _ in range(args.warmup):
+        umi.detrend_batched(flux, batch.offsets, W, trend=trend, detr=detr)
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = umi.kernel_launch_count()
+    barrier(dist)
+    torch.cuda.synchronize()
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for s in range(args.steps):
+        flush.fill_(float(s))          # L2 flush between steps (inside the timed region)
+        starts[s].record(stream)
+        umi.detrend_batched(flux, batch.offsets, W, trend=trend, detr=detr)
+        ends[s].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    gpu_launches = umi.kernel_launch_count() - launches0
+    clk = clocks.stop()
+    elapsed_ms = t_all0.elapsed_time(t_all1)
+    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(starts, ends)]))
+    elapsed_ms = max_over_ranks(dist, elapsed_ms, dev)
+    total_evals = evals * world
+    value = total_evals * args.steps / (elapsed_ms / 1e3)
+
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = sms * LANES_PER_SM * sm_max * 1e6 / 1e12      # T lane-ops/s
+    achieved = OPS_PER_SAMPLE * samples / (kernel_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tlane-op/s",
+                "frac": achieved / peak_ops, "traffic": None,
+                "note": "peak = %d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz); achieved = %d lane-ops x "
+                        "%.4g valid window samples / mean kernel time %.3f ms"
+                        % (sms, sm_max, peak_src, OPS_PER_SAMPLE, samples, kernel_ms)}
+
+    line = {
+        "metric": "window-evals/s", "value": value, "unit": "window-evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "%d TESS-like 2-min curves x %d samples, W=361, alpha 2, c 5, 5 iters, "
+                               "batched persistent kernel (CUDA graph)" % (batch.B, args.n),
+                   "global_batch": batch.B * world, "seq_len": args.n, "parallelism": "dp%d" % world,
+                   "l2": "flushed between steps (%d MB write)" % (flush.numel() * 4 >> 20)},
+        "curves_per_s": batch.B * world * args.steps / (elapsed_ms / 1e3),
+        "kernel_ms": kernel_ms,
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": gpu_launches,
+    }
+
+    if not args.no_extras and rank == 0:
+        line["per_curve_launch"] = per_curve_leg(umi, torch, flux, batch, W, evals)
+        line["e2e"] = e2e_leg(umi, torch, batch, W, evals, args)
+        line["serving"] = serving_leg(umi, torch, dev, args)
+        line["cpu_baseline"] = cpu_baseline(batch, W)
+    elif rank == 0:
+        line["e2e"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def per_curve_leg(umi, torch, flux, batch, W, evals):
+    """The plain form: one umi_detrend launch per curve on one stream."""
+    trend = torch.empty_like(flux)
+    detr = torch.empty_like(flux)
+    views = [(flux[batch.offsets[b]:batch.offsets[b + 1]], trend[batch.offsets[b]:batch.offsets[b + 1]],
+              detr[batch.offsets[b]:batch.offsets[b + 1]]) for b in range(batch.B)]
+    for x, t, d in views[:8]:
+        umi.detrend(x, int(W[0]), trend=t, detr=d)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for b, (x, t, d) in enumerate(views):
+        umi.detrend(x, int(W[b]), trend=t, detr=d)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": evals / (ms / 1e3), "unit": "window-evals/s", "curves_per_s": batch.B / (ms / 1e3),
+            "ms": ms, "launches": batch.B}
+
+
+def e2e_leg(umi, torch, batch, W, evals, args):
+    """Same metric through the host-buffer entry point (copies inside)."""
+    fh = torch.from_numpy(batch.flux).pin_memory()
+    th = torch.empty(batch.flux.size, dtype=torch.float32).pin_memory()
+    dh = torch.empty(batch.flux.size, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        umi.detrend_batched_host(fh, batch.offsets, W, trend=th, detr=dh)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        umi.detrend_batched_host(fh, batch.offsets, W, trend=th, detr=dh)
+    dt = time.perf_counter() - t0
+    nbytes = batch.flux.size * 4
+    return {"value": evals * steps / dt, "unit": "window-evals/s", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": 2 * nbytes, "steps": steps,
+            "curves_per_s": batch.B * steps / dt}
+
+
+def serving_leg(umi, torch, dev, args):
+    """Poisson arrivals of mixed-size curves into the continuous-batching
+    server (inputs resident on the device), against serialized per-curve
+    launches of the same requests."""
+    from paper_2604_06602_gb300 import synth
+    arrivals, pool, which, cads, kinds = synth.serving_requests(
+        n_requests=args.serve_requests, rate_hz=args.serve_rate, max_distinct=96)
+    Ws = [umi.window_length(c) for c in cads]
+    dev_pool = [torch.from_numpy(x).to(dev) for x in pool]
+    torch.cuda.synchronize()
+    lat = []
+    with umi.Server(mem_budget_bytes=40 << 30, n_streams=4, max_batch_curves=512) as srv:
+        # warm up the kernels once
+        t = srv.submit(dev_pool[0], Ws[0])
+        srv.wait(t, 60)
+        srv.release(t)
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(args.serve_requests):
+            due = t0 + arrivals[i]
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 2e-4:
+                    time.sleep(min(1e-3, due - now - 1e-4))
+            k = int(which[i])
+            tickets.append(srv.submit(dev_pool[k], Ws[k]))
+            # release finished results as they come (results stay until polled)
+            while len(tickets) > 0 and srv.poll(tickets[0]) is not None:
+                tt = tickets.pop(0)
+                lat.append(srv.poll(tt)[2])
+                srv.release(tt)
+        for tt in tickets:
+            srv.wait(tt, 120)
+            lat.append(srv.poll(tt)[2])
+            srv.release(tt)
+        t_total = time.perf_counter() - t0
+        stats = srv.stats()
+    # Serialized per-curve launches of the same request sequence, one stream.
+    trend = [torch.empty_like(x) for x in dev_pool]
+    detr = [torch.empty_like(x) for x in dev_pool]
+    nser = min(args.serve_requests, 1000)
+    torch.cuda.synchronize()
+    s0 = time.perf_counter()
+    for i in range(nser):
+        k = int(which[i])
+        umi.detrend(dev_pool[k], Ws[k], trend=trend[k], detr=detr[k])
+    torch.cuda.synchronize()
+    ser_dt = time.perf_counter() - s0
+    lat = np.array(lat)
+    return {"requests": args.serve_requests, "offered_rate_hz": args.serve_rate,
+            "curves_per_s": args.serve_requests / t_total,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_batch_curves": stats["mean_batch_curves"], "batches": stats["batches_launched"],
+            "serialized_per_curve_curves_per_s": nser / ser_dt,
+            "mixture": "45% TESS 2-min N 5k-20k W=361, 45% Kepler N 4k-70k W=25, 10% 20-s N 60k-118k W=2161"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_umi(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

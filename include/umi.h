@@ -1,0 +1,268 @@
+/*
+ * umi.h -- C ABI of libumi, the GB300 (sm_103a) implementation of UMI, the
+ * sliding-window asymmetric robust trend of arXiv 2604.06602 ("UMI: A
+ * GPU-Accelerated Asymmetric Robust Estimator for Photometric Detrending").
+ *
+ * What every detrend entry point computes (Section 2 of the paper):
+ *   for each sample position j of a light curve x[0..n):
+ *     window   the W samples x[j-h .. j+h], h = (W-1)/2, truncated at the ends
+ *              of the curve; non-finite samples are missing and are dropped;
+ *     Phase 1  m = exact median of the valid window samples (Section 2.1);
+ *              for an even count the lower median, rank floor((n_valid-1)/2);
+ *     Phase 2  s = 0.6745 * sqrt(mean over x > m of (x - m)^2)  (Eq. 1);
+ *     Phase 3  mu = m, then `iters` times: u = (x - mu)/(c s),
+ *              u_eff = alpha u if u < 0 else u (Eq. 2),
+ *              w = (1 - u_eff^2)^2 if |u_eff| < 1 else 0 (Eq. 3),
+ *              mu <- sum(w x)/sum(w) (Eq. 4; mu kept if sum(w) == 0);
+ *     output   trend[j] = mu, detr[j] = x[j] / mu.
+ *   If no sample lies above m, or s == 0, the trend is m.  Positions whose
+ *   own sample is missing, or whose window holds fewer than min_valid valid
+ *   samples, get NaN in both outputs.
+ *
+ * Arithmetic: FP32 on the GPU.  Medians and the set of above-median samples
+ * are exact (they are comparisons of the FP32 inputs); the trend agrees with
+ * an FP64 evaluation of the same definition to about 1e-6 relative for
+ * flux-like data.  Finite input samples must satisfy |x| < 2^60; larger
+ * magnitudes overflow the FP32 sums of Eq. 1 and give unspecified results.
+ *
+ * Conventions for every call below:
+ *   - `_d` pointers are CUDA device pointers (any allocator), `_h` pointers
+ *     are host pointers.  All buffers stay owned by the caller.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *     is enqueued on it; the call returns without waiting for the GPU unless
+ *     the entry point says otherwise.  Results are valid once the stream has
+ *     reached the end of the enqueued work.
+ *   - Arguments are validated on the host before anything is enqueued; an
+ *     invalid argument returns UMI_ERR_INVALID_ARG and enqueues nothing.
+ *     Errors are returned, never raised by abort().  umi_last_error() gives a
+ *     message for the calling thread's most recent failure.
+ *   - Calls are thread-safe.  Calls on different streams may overlap.
+ */
+#ifndef UMI_H
+#define UMI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    UMI_OK = 0,
+    UMI_ERR_INVALID_ARG = 1,    /* an argument failed validation; nothing enqueued */
+    UMI_ERR_CUDA = 2,           /* a CUDA runtime call failed (see umi_last_error) */
+    UMI_ERR_OOM = 3,            /* device or host allocation failed */
+    UMI_ERR_BUSY = 4,           /* server: the request can never fit the budget / slots */
+    UMI_ERR_NOT_READY = 5,      /* server: the result is not finished yet */
+    UMI_ERR_TIMEOUT = 6,        /* a bounded host-side wait ran out */
+    UMI_ERR_UNKNOWN_TICKET = 7, /* server: no such ticket (never issued or released) */
+    UMI_ERR_FAILED = 8          /* server: the request's batch failed; others unaffected */
+} umi_status;
+
+/* Estimator parameters (Section 2.3; presets in Section 4, Table 4). */
+typedef struct {
+    float alpha;       /* asymmetry of Eq. 2, > 0; 2.0 default (TESS), 3.0 Kepler,
+                          1.0 symmetric biweight, 10.0 with c = 2.5 aggressive */
+    float c;           /* tuning constant of the standardised residual, > 0; 5.0 */
+    int32_t iters;     /* fixed number of Phase 3 iterations, >= 0; 5 */
+    int32_t min_valid; /* minimum valid samples per window for an output; -1 means
+                          floor(W/3) (the W/3 rule of Section 4, Kepler Long-Cadence);
+                          0 disables the check */
+} umi_params;
+
+/* Fill `p` with alpha 2, c 5, iters 5, min_valid -1.  NULL is ignored. */
+void umi_default_params(umi_params *p);
+
+/*
+ * Window length in samples for a cadence and a window span, both in days:
+ * W = round(window_days / cadence_days) | 1 (Section 2 opening paragraph;
+ * the bracket printed there is read as round-to-nearest, so that a cadence
+ * recovered from time stamps with rounding error still gives 361 for
+ * TESS 2-min data).  Returns W >= 1, or -1 for a non-positive or non-finite
+ * argument or a ratio above 1e9.  Host only; never touches the GPU.
+ */
+int32_t umi_window_length(double cadence_days, double window_days);
+
+/*
+ * One light curve (Section 2; one launch).
+ *   flux_d   [n] FP32 samples on the device; non-finite = missing
+ *   n        number of samples, >= 0 (n == 0 returns UMI_OK and enqueues nothing)
+ *   W        window length, odd, 1 <= W <= umi_max_window()
+ *   params   NULL means umi_default_params()
+ *   trend_d, detr_d  [n] FP32 outputs on the device (may not alias flux_d)
+ * Allocates no device memory.  Asynchronous on `stream`.
+ */
+umi_status umi_detrend(const float *flux_d, int64_t n, int32_t W, const umi_params *params,
+                       float *trend_d, float *detr_d, void *stream);
+
+/*
+ * Many light curves of any lengths and window lengths in one persistent
+ * launch per window band (Section 2.6 runs one thread per (star, position);
+ * here CTAs pull (curve, tile) work items from a device queue).
+ *   flux_d     CSR samples on the device: curve b is flux_d[offsets_h[b] ..
+ *              offsets_h[b+1]); outputs use the same layout
+ *   offsets_h  [B+1] host array, offsets_h[0] == 0, non-decreasing
+ *   W_h        [B] host array of odd window lengths, one per curve
+ *   B          number of curves, >= 0
+ *   params     shared by all curves; NULL means defaults
+ * Device scratch (the work queue, a few bytes per tile) comes from the
+ * stream-ordered allocator (cudaMallocAsync) on `stream` and is released on
+ * the same stream.  Asynchronous on `stream`.  Equal-shaped batches replay a
+ * cached CUDA graph (see umi_set_graph_cache).
+ */
+umi_status umi_detrend_batched(const float *flux_d, const int64_t *offsets_h, const int32_t *W_h,
+                               int32_t B, const umi_params *params, float *trend_d,
+                               float *detr_d, void *stream);
+
+/*
+ * umi_detrend_batched on HOST buffers: copies flux_h to the device, runs the
+ * batched path and copies trend_h / detr_h back, all on `stream`, and waits
+ * for the stream before returning.  Device buffers come from
+ * cudaMallocAsync and are freed before return.  Pinned host memory makes the
+ * copies asynchronous DMA; pageable memory works but is slower.
+ */
+umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_h,
+                                    const int32_t *W_h, int32_t B, const umi_params *params,
+                                    float *trend_h, float *detr_h, void *stream);
+
+/*
+ * Diagnostic form of umi_detrend, for parity checks.  Besides trend and
+ * detr it writes, per position:
+ *   median_d  the window median (also where the output is NaN), NaN for an
+ *             empty window
+ *   nvalid_d  valid samples in the window
+ *   nplus_d   samples strictly above the median (the support of Eq. 1)
+ *   scale_d   s of Eq. 1 (times 0.6745) where the trend is produced, else NaN
+ * Any of the four may be NULL.  Same ownership and ordering as umi_detrend.
+ */
+umi_status umi_detrend_diag(const float *flux_d, int64_t n, int32_t W, const umi_params *params,
+                            float *trend_d, float *detr_d, float *median_d, int32_t *nvalid_d,
+                            int32_t *nplus_d, float *scale_d, void *stream);
+
+/* Largest supported window length (odd). */
+int32_t umi_max_window(void);
+
+/*
+ * Kernel plan chosen for a window length and a problem size (positions to
+ * evaluate), for inspection and tuning.  `lanes` = lanes per window (1-32),
+ * `slots` = register slots per lane, `chain` = consecutive positions per lane
+ * group, `threads` = threads per CTA.
+ */
+typedef struct {
+    int32_t lanes;
+    int32_t slots;
+    int32_t chain;
+    int32_t threads;
+    int32_t variant; /* index into the compiled variant table */
+} umi_plan;
+
+umi_status umi_get_plan(int32_t W, int64_t positions, umi_plan *plan);
+
+/*
+ * Autotuner.  Times every eligible (lanes, slots, chain, threads) choice for
+ * window length W on a synthetic flux-like curve of `positions` samples on
+ * `stream` (blocking), and records the fastest for W's band.  Later calls
+ * use the recorded plan.  umi_save_tuning / umi_load_tuning persist the
+ * table as text keyed by GPU name.
+ */
+umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *best,
+                        double *best_ms);
+umi_status umi_save_tuning(const char *path);
+umi_status umi_load_tuning(const char *path);
+void umi_clear_tuning(void);
+
+/* Enable (1) or disable (0) the CUDA-graph cache of umi_detrend_batched. */
+void umi_set_graph_cache(int enabled);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of detrend requests under a device-memory
+ * budget.  A scheduler thread admits queued requests while their resident
+ * bytes (flux + trend + detr, 12 bytes per sample, plus alignment) fit the
+ * budget and a slot is free, gathers the admitted requests into batched
+ * launches on `n_streams` streams so that batches overlap on the GPU, and
+ * marks each request done when its batch's completion event fires.  Results
+ * stay on the device until released.
+ * ------------------------------------------------------------------------ */
+typedef struct umi_server umi_server;
+
+typedef struct {
+    uint64_t mem_budget_bytes; /* resident request memory (default 40 GiB) */
+    int32_t max_slots;         /* resident requests at most (default 65536) */
+    int32_t n_streams;         /* batches in flight at most (default 4) */
+    int32_t max_batch_curves;  /* curves per launch at most (default 1024) */
+    int32_t device;            /* CUDA device ordinal (default 0) */
+    double max_wait_s;         /* longest a request waits to be batched while a
+                                  stream is idle (default 0: launch at once) */
+} umi_server_config;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, failed, rejected, released;
+    uint64_t batches_launched;
+    uint64_t resident_bytes, peak_resident_bytes;
+    uint64_t queued_requests;
+    double mean_batch_curves;
+} umi_server_stats;
+
+void umi_server_default_config(umi_server_config *cfg);
+
+/* Creates the server and its arena (one cudaMalloc of mem_budget_bytes). */
+umi_status umi_server_create(const umi_server_config *cfg, umi_server **out);
+
+/*
+ * Queue one curve.  `flux` is a host pointer (is_device_ptr == 0) or a device
+ * pointer (1); it is copied into server memory during admission, so the
+ * caller may reuse its buffer once the ticket is done (host buffers: once
+ * this call returns, because host data are copied into a staging buffer
+ * first).  Returns UMI_ERR_BUSY if the request can never fit the budget,
+ * UMI_ERR_INVALID_ARG for bad W/n/params.  `ticket` receives a non-zero id.
+ */
+umi_status umi_server_submit(umi_server *s, const float *flux, int is_device_ptr, int64_t n,
+                             int32_t W, const umi_params *params, uint64_t *ticket);
+
+/*
+ * Non-blocking.  UMI_OK when done: *trend_d / *detr_d (device pointers into
+ * server memory, valid until umi_server_release) and *latency_s (submit to
+ * completion) are filled (any may be NULL).  UMI_ERR_NOT_READY while queued
+ * or running, UMI_ERR_FAILED if its batch failed.
+ */
+umi_status umi_server_poll(umi_server *s, uint64_t ticket, const float **trend_d,
+                           const float **detr_d, double *latency_s);
+
+/* Blocks until the ticket is done or failed, or timeout_s passes. */
+umi_status umi_server_wait(umi_server *s, uint64_t ticket, double timeout_s);
+
+/* Copies a finished result to host buffers of n floats (either may be NULL). */
+umi_status umi_server_copy_out(umi_server *s, uint64_t ticket, float *trend_h, float *detr_h);
+
+/* Frees the ticket's device memory; the pointers from poll become invalid. */
+umi_status umi_server_release(umi_server *s, uint64_t ticket);
+
+umi_status umi_server_get_stats(umi_server *s, umi_server_stats *out);
+
+/*
+ * Host-side fault injection for tests (no GPU fault is ever involved):
+ * kind 1 makes the next `count` batches fail before launch (their requests
+ * end UMI_ERR_FAILED), kind 2 makes the next `count` admissions fail as if
+ * the arena allocation had failed.  Other requests are unaffected.
+ */
+umi_status umi_server_inject_fault(umi_server *s, int kind, int count);
+
+/* Waits for in-flight batches, then frees everything. */
+void umi_server_destroy(umi_server *s);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *umi_last_error(void);
+
+/* Library version string. */
+const char *umi_version(void);
+
+/* Number of kernels libumi has launched in this process (all entry points;
+ * a graph replay counts the kernels it contains).  For launch accounting. */
+long long umi_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UMI_H */

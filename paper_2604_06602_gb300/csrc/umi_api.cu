@@ -1,0 +1,855 @@
+// umi_api.cu -- the C ABI of libumi: validation, planning, launches, the
+// batched work queue, the CUDA-graph cache and the autotuner.
+//
+// The estimator is Section 2 of the paper (window rule; Phase 1 median;
+// Phase 2 upper-RMS scale, Eq. 1; Phase 3 asymmetric bisquare, Eqs. 2-4);
+// the device code is umi_kernel.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <list>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "umi_internal.h"
+
+namespace umi {
+
+// ---------------------------------------------------------------- errors --
+static thread_local std::string t_error;
+
+umi_status fail(umi_status st, const std::string &msg)
+{
+    t_error = msg;
+    return st;
+}
+
+umi_status fail_cuda(cudaError_t err, const char *what)
+{
+    t_error = std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+    return err == cudaErrorMemoryAllocation ? UMI_ERR_OOM : UMI_ERR_CUDA;
+}
+
+void clear_error() { t_error.clear(); }
+
+#define UMI_CUDA(call, what)                         \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return fail_cuda(e_, what); \
+    } while (0)
+
+// ----------------------------------------------------------- device info --
+static std::mutex g_dev_mu;
+
+int current_device()
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) return -1;
+    return d;
+}
+
+const DeviceInfo &device_info(int device)
+{
+    static std::map<int, DeviceInfo> cache;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    auto it = cache.find(device);
+    if (it != cache.end()) return it->second;
+    DeviceInfo di;
+    di.device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) {
+        di.sms = prop.multiProcessorCount;
+        di.smem_optin = prop.sharedMemPerBlockOptin;
+        di.name = prop.name;
+    }
+    return cache.emplace(device, di).first->second;
+}
+
+// ------------------------------------------------------------- planning --
+static const int kMaxWindow = 4095;
+
+bool legal_chain(int G, int chain)
+{
+    // Groups of one warp start G*chain/G... apart in the tile; a chain of
+    // G * odd positions puts the 32/G groups of a warp on disjoint banks.
+    if (chain < 1) return false;
+    if (G >= 32) return true;
+    return chain % G == 0 && ((chain / G) & 1) == 1;
+}
+
+static int round_chain(int G, int target)
+{
+    if (G >= 32) return std::max(1, target);
+    int odd = std::max(1, target / G);
+    if ((odd & 1) == 0) odd += 1;
+    return G * odd;
+}
+
+static int default_threads(int G) { return G <= 2 ? 128 : 256; }
+static int default_chain(int G)
+{
+    switch (G) {
+    case 1: return 33;
+    case 2: return 34;
+    case 4: return 36;
+    case 8: return 40;
+    case 16: return 48;
+    default: return 64;
+    }
+}
+
+// Tuned plans, keyed by window length (filled by umi_autotune / umi_load_tuning).
+static std::mutex g_tune_mu;
+static std::map<int, Plan> g_tuned;
+
+static int pick_variant(int W)
+{
+    int n = 0;
+    const Variant *t = variant_table(&n);
+    for (int v = 0; v < n; ++v)
+        if (t[v].G * t[v].R >= W) return v;
+    return -1;
+}
+
+umi_status make_plan(int W, int64_t positions, Plan *plan)
+{
+    if (W < 1 || W > kMaxWindow || (W % 2) == 0)
+        return fail(UMI_ERR_INVALID_ARG, "W must be odd and in [1, " + std::to_string(kMaxWindow) + "]");
+    int n = 0;
+    const Variant *t = variant_table(&n);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(W);
+        if (it != g_tuned.end()) {
+            Plan p = it->second;
+            // A tuned plan sized for large batches is kept for small work too,
+            // except that the chain shrinks so the GPU still fills up.
+            if (positions > 0) {
+                const int sms = device_info(current_device()).sms;
+                const int64_t groups = std::max<int64_t>(1, (int64_t)sms * 4 * (p.threads / p.G));
+                const int64_t want = (positions + groups - 1) / groups;
+                if (want < p.chain) p.chain = round_chain(p.G, (int)want);
+            }
+            *plan = p;
+            return UMI_OK;
+        }
+    }
+    const int v = pick_variant(W);
+    if (v < 0) return fail(UMI_ERR_INVALID_ARG, "no kernel variant for W=" + std::to_string(W));
+    Plan p;
+    p.variant = v;
+    p.G = t[v].G;
+    p.R = t[v].R;
+    p.threads = default_threads(p.G);
+    p.chain = default_chain(p.G);
+    if (positions > 0) {
+        // Small problems: shorten the chain so that about 4 CTAs per SM exist.
+        const int sms = std::max(1, device_info(current_device()).sms);
+        const int64_t groups = (int64_t)sms * 4 * (p.threads / p.G);
+        const int64_t want = (positions + groups - 1) / groups;
+        if (want < p.chain) p.chain = round_chain(p.G, (int)want);
+    }
+    *plan = p;
+    return UMI_OK;
+}
+
+int resolve_min_valid(int W, int min_valid) { return min_valid < 0 ? W / 3 : min_valid; }
+
+umi_status check_params(const umi_params *p, umi_params *out)
+{
+    umi_params q;
+    umi_default_params(&q);
+    if (p) q = *p;
+    if (!(q.alpha > 0.f) || !std::isfinite(q.alpha))
+        return fail(UMI_ERR_INVALID_ARG, "alpha must be a positive finite number");
+    if (!(q.c > 0.f) || !std::isfinite(q.c))
+        return fail(UMI_ERR_INVALID_ARG, "c must be a positive finite number");
+    if (q.iters < 0 || q.iters > 1000) return fail(UMI_ERR_INVALID_ARG, "iters must be in [0, 1000]");
+    if (q.min_valid < -1) return fail(UMI_ERR_INVALID_ARG, "min_valid must be >= -1");
+    *out = q;
+    return UMI_OK;
+}
+
+static std::mutex g_attr_mu;
+
+umi_status prepare_kernel(const Plan &plan, bool diag)
+{
+    int n = 0;
+    const Variant *t = variant_table(&n);
+    if (plan.variant < 0 || plan.variant >= n) return fail(UMI_ERR_INVALID_ARG, "bad plan");
+    const size_t smem = plan.smem_bytes();
+    const DeviceInfo &di = device_info(current_device());
+    if (smem > di.smem_optin)
+        return fail(UMI_ERR_INVALID_ARG, "tile needs more shared memory than the device allows");
+    if (smem > 48 * 1024) {
+        std::lock_guard<std::mutex> lk(g_attr_mu);
+        const void *k = diag ? t[plan.variant].kernel_diag : t[plan.variant].kernel;
+        UMI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                 "cudaFuncSetAttribute");
+    }
+    return UMI_OK;
+}
+
+int persistent_grid(const Plan &plan, bool diag)
+{
+    int n = 0;
+    const Variant *t = variant_table(&n);
+    const void *k = diag ? t[plan.variant].kernel_diag : t[plan.variant].kernel;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, plan.threads, plan.smem_bytes()) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int sms = std::max(1, device_info(current_device()).sms);
+    return sms * per_sm;
+}
+
+static Curve make_curve(const float *flux, float *trend, float *detr, int64_t n, int W,
+                        const umi_params &p)
+{
+    Curve c;
+    c.flux = flux;
+    c.trend = trend;
+    c.detr = detr;
+    c.n = n;
+    c.W = W;
+    c.min_valid = resolve_min_valid(W, p.min_valid);
+    c.alpha = p.alpha;
+    c.c = p.c;
+    c.iters = p.iters;
+    c.reserved = 0;
+    return c;
+}
+
+// -------------------------------------------------------- single curve --
+static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const umi_params *params,
+                                 float *trend, float *detr, const Diag *diag, cudaStream_t stream)
+{
+    clear_error();
+    umi_params p;
+    umi_status st = check_params(params, &p);
+    if (st != UMI_OK) return st;
+    if (n < 0) return fail(UMI_ERR_INVALID_ARG, "n must be >= 0");
+    if (W < 1 || (W % 2) == 0 || W > kMaxWindow)
+        return fail(UMI_ERR_INVALID_ARG, "W must be odd and in [1, " + std::to_string(kMaxWindow) + "]");
+    if (n == 0) return UMI_OK;
+    if (!flux || !trend || !detr) return fail(UMI_ERR_INVALID_ARG, "null buffer");
+    Plan plan;
+    st = make_plan(W, n, &plan);
+    if (st != UMI_OK) return st;
+    const bool use_diag = diag != nullptr;
+    st = prepare_kernel(plan, use_diag);
+    if (st != UMI_OK) return st;
+    const int64_t T = plan.tile();
+    const int64_t items = (n + T - 1) / T;
+    if (items > INT32_MAX) return fail(UMI_ERR_INVALID_ARG, "curve too long");
+    LaunchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.curves = nullptr;
+    a.single = make_curve(flux, trend, detr, n, W, p);
+    a.items = nullptr;
+    a.n_items = (int32_t)items;
+    a.chain = plan.chain;
+    a.queue = nullptr;
+    if (diag) a.diag = *diag;
+    int nv = 0;
+    const Variant *t = variant_table(&nv);
+    LaunchFn fn = use_diag ? t[plan.variant].launch_diag : t[plan.variant].launch;
+    cudaError_t e = fn(a, (int)items, plan.threads, plan.smem_bytes(), stream);
+    if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
+    return UMI_OK;
+}
+
+// ------------------------------------------------------------- batches --
+umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout)
+{
+    int nvar = 0;
+    variant_table(&nvar);
+    // One band per distinct plan (variant, chain, threads), in descending
+    // slot capacity so that the heaviest tiles start first.
+    std::map<std::tuple<int, int, int>, std::vector<int>> by_plan;
+    std::vector<Plan> plans;
+    for (size_t b = 0; b < curves.size(); ++b) {
+        Plan p;
+        umi_status st = make_plan(curves[b].W, -1, &p);
+        if (st != UMI_OK) return st;
+        by_plan[std::make_tuple(-p.G * p.R, p.chain, p.threads)].push_back((int)b);
+        plans.push_back(p);
+    }
+    layout->bands.clear();
+    layout->items.clear();
+    for (auto &kv : by_plan) {
+        BatchLayout::Band band;
+        band.plan = plans[kv.second.front()];
+        band.first_item = (int32_t)layout->items.size();
+        const int64_t T = band.plan.tile();
+        // Longest curves first: their tiles are interleaved with others by the
+        // queue anyway, but this keeps the tail short.
+        std::vector<int> order = kv.second;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return curves[a].n > curves[b].n; });
+        for (int b : order) {
+            const int64_t tiles = (curves[b].n + T - 1) / T;
+            for (int64_t k = 0; k < tiles; ++k) {
+                if (layout->items.size() >= (size_t)INT32_MAX)
+                    return fail(UMI_ERR_INVALID_ARG, "too many work items");
+                layout->items.push_back(Item{(int32_t)b, (int32_t)k});
+            }
+        }
+        band.n_items = (int32_t)layout->items.size() - band.first_item;
+        if (band.n_items > 0) layout->bands.push_back(band);
+    }
+    return UMI_OK;
+}
+
+// Device scratch for one batch: [curve table][items][one counter per band].
+struct Scratch {
+    size_t curve_off = 0, item_off = 0, counter_off = 0, bytes = 0;
+};
+
+static Scratch scratch_layout(size_t n_curves, size_t n_items, size_t n_bands)
+{
+    Scratch s;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    s.curve_off = 0;
+    s.item_off = up(n_curves * sizeof(Curve));
+    s.counter_off = s.item_off + up(n_items * sizeof(Item));
+    s.bytes = s.counter_off + up(std::max<size_t>(1, n_bands) * sizeof(int32_t));
+    return s;
+}
+
+static umi_status enqueue_bands(const BatchLayout &lay, char *dev, const Scratch &sc,
+                                cudaStream_t stream, int *launches)
+{
+    int nv = 0;
+    const Variant *t = variant_table(&nv);
+    UMI_CUDA(cudaMemsetAsync(dev + sc.counter_off, 0, lay.bands.size() * sizeof(int32_t), stream),
+             "cudaMemsetAsync");
+    int count = 0;
+    for (size_t k = 0; k < lay.bands.size(); ++k) {
+        const BatchLayout::Band &band = lay.bands[k];
+        LaunchArgs a;
+        memset(&a, 0, sizeof(a));
+        a.curves = reinterpret_cast<const Curve *>(dev + sc.curve_off);
+        a.items = reinterpret_cast<const Item *>(dev + sc.item_off) + band.first_item;
+        a.n_items = band.n_items;
+        a.chain = band.plan.chain;
+        a.queue = reinterpret_cast<int32_t *>(dev + sc.counter_off) + k;
+        const int grid = std::min(band.n_items, persistent_grid(band.plan, false));
+        cudaError_t e = t[band.plan.variant].launch(a, grid, band.plan.threads,
+                                                    band.plan.smem_bytes(), stream);
+        if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
+        ++count;
+    }
+    if (launches) *launches = count;
+    return UMI_OK;
+}
+
+umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream, int *launches)
+{
+    if (launches) *launches = 0;
+    if (curves.empty()) return UMI_OK;
+    BatchLayout lay;
+    umi_status st = build_layout(curves, &lay);
+    if (st != UMI_OK) return st;
+    if (lay.items.empty()) return UMI_OK;
+    for (const auto &band : lay.bands) {
+        st = prepare_kernel(band.plan, false);
+        if (st != UMI_OK) return st;
+    }
+    const Scratch sc = scratch_layout(curves.size(), lay.items.size(), lay.bands.size());
+    // Host staging in one block so a single copy moves the tables.
+    std::vector<char> host(sc.counter_off);
+    memcpy(host.data() + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
+    memcpy(host.data() + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
+    void *dev = nullptr;
+    UMI_CUDA(cudaMallocAsync(&dev, sc.bytes, stream), "cudaMallocAsync");
+    // Pageable source: the call returns once the data are staged, so `host`
+    // may go out of scope afterwards.
+    cudaError_t e = cudaMemcpyAsync(dev, host.data(), sc.counter_off, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(dev, stream);
+        return fail_cuda(e, "cudaMemcpyAsync");
+    }
+    st = enqueue_bands(lay, (char *)dev, sc, stream, launches);
+    cudaError_t ef = cudaFreeAsync(dev, stream);
+    if (st != UMI_OK) return st;
+    if (ef != cudaSuccess) return fail_cuda(ef, "cudaFreeAsync");
+    return UMI_OK;
+}
+
+// ---------------------------------------------------- CUDA-graph cache --
+// Equal-shaped batches (same buffers, offsets, windows and parameters)
+// replay a captured graph whose work-queue tables live in persistent device
+// memory, so the steady state costs one graph launch and no host planning.
+struct GraphEntry {
+    uint64_t key = 0;
+    std::vector<int64_t> offsets;
+    std::vector<int32_t> W;
+    const float *flux = nullptr;
+    float *trend = nullptr, *detr = nullptr;
+    umi_params params{};
+    int device = -1;
+    void *dev = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+};
+
+static std::mutex g_graph_mu;
+static std::list<GraphEntry> g_graphs;  // most recent first
+static std::atomic<int> g_graph_enabled{1};
+static const size_t kMaxGraphs = 8;
+
+static uint64_t fnv1a(const void *data, size_t n, uint64_t h)
+{
+    const unsigned char *p = (const unsigned char *)data;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static void destroy_entry(GraphEntry &g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.dev) cudaFree(g.dev);  // synchronises with prior work using it
+    g.exec = nullptr;
+    g.dev = nullptr;
+}
+
+static umi_status build_graph(const std::vector<Curve> &curves, GraphEntry *g)
+{
+    BatchLayout lay;
+    umi_status st = build_layout(curves, &lay);
+    if (st != UMI_OK) return st;
+    for (const auto &band : lay.bands) {
+        st = prepare_kernel(band.plan, false);
+        if (st != UMI_OK) return st;
+    }
+    const Scratch sc = scratch_layout(curves.size(), lay.items.size(), lay.bands.size());
+    std::vector<char> host(sc.counter_off);
+    memcpy(host.data() + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
+    if (!lay.items.empty())
+        memcpy(host.data() + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
+    UMI_CUDA(cudaMalloc(&g->dev, sc.bytes), "cudaMalloc (graph tables)");
+    UMI_CUDA(cudaMemcpy(g->dev, host.data(), sc.counter_off, cudaMemcpyHostToDevice), "cudaMemcpy");
+    cudaStream_t cs;
+    UMI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return fail_cuda(e, "cudaStreamBeginCapture");
+    }
+    umi_status est = enqueue_bands(lay, (char *)g->dev, sc, cs, &g->launches);
+    e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (est != UMI_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return est;
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGraphInstantiate");
+    return UMI_OK;
+}
+
+static std::atomic<long long> g_kernel_launches{0};
+
+static umi_status batched_impl(const float *flux, const int64_t *offsets, const int32_t *W,
+                               int32_t B, const umi_params *params, float *trend, float *detr,
+                               cudaStream_t stream, bool allow_graph)
+{
+    clear_error();
+    umi_params p;
+    umi_status st = check_params(params, &p);
+    if (st != UMI_OK) return st;
+    if (B < 0) return fail(UMI_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return UMI_OK;
+    if (!offsets || !W) return fail(UMI_ERR_INVALID_ARG, "null offsets or W");
+    if (offsets[0] != 0) return fail(UMI_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int32_t b = 0; b < B; ++b) {
+        if (offsets[b + 1] < offsets[b]) return fail(UMI_ERR_INVALID_ARG, "offsets must be non-decreasing");
+        if (W[b] < 1 || (W[b] % 2) == 0 || W[b] > kMaxWindow)
+            return fail(UMI_ERR_INVALID_ARG, "W[" + std::to_string(b) + "] must be odd and in [1, " +
+                                                 std::to_string(kMaxWindow) + "]");
+    }
+    if (offsets[B] == 0) return UMI_OK;
+    if (!flux || !trend || !detr) return fail(UMI_ERR_INVALID_ARG, "null buffer");
+    std::vector<Curve> curves;
+    curves.reserve(B);
+    for (int32_t b = 0; b < B; ++b) {
+        const int64_t o = offsets[b], n = offsets[b + 1] - offsets[b];
+        if (n == 0) continue;
+        curves.push_back(make_curve(flux + o, trend + o, detr + o, n, W[b], p));
+    }
+    if (!allow_graph || !g_graph_enabled.load()) {
+        int launches = 0;
+        st = launch_curve_table(curves, stream, &launches);
+        g_kernel_launches += launches;
+        return st;
+    }
+    const int dev = current_device();
+    uint64_t key = 1469598103934665603ull;
+    key = fnv1a(offsets, sizeof(int64_t) * (B + 1), key);
+    key = fnv1a(W, sizeof(int32_t) * B, key);
+    key = fnv1a(&p, sizeof(p), key);
+    key = fnv1a(&flux, sizeof(flux), key);
+    key = fnv1a(&trend, sizeof(trend), key);
+    key = fnv1a(&detr, sizeof(detr), key);
+    key = fnv1a(&dev, sizeof(dev), key);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+        GraphEntry &g = *it;
+        if (g.key != key || g.device != dev || g.flux != flux || g.trend != trend || g.detr != detr ||
+            (int32_t)g.W.size() != B || memcmp(&g.params, &p, sizeof(p)) != 0 ||
+            memcmp(g.offsets.data(), offsets, sizeof(int64_t) * (B + 1)) != 0 ||
+            memcmp(g.W.data(), W, sizeof(int32_t) * B) != 0)
+            continue;
+        UMI_CUDA(cudaGraphLaunch(g.exec, stream), "cudaGraphLaunch");
+        g_kernel_launches += g.launches;
+        g_graphs.splice(g_graphs.begin(), g_graphs, it);
+        return UMI_OK;
+    }
+    GraphEntry g;
+    g.key = key;
+    g.offsets.assign(offsets, offsets + B + 1);
+    g.W.assign(W, W + B);
+    g.flux = flux;
+    g.trend = trend;
+    g.detr = detr;
+    g.params = p;
+    g.device = dev;
+    st = build_graph(curves, &g);
+    if (st != UMI_OK) {
+        destroy_entry(g);
+        return st;
+    }
+    cudaError_t e = cudaGraphLaunch(g.exec, stream);
+    if (e != cudaSuccess) {
+        destroy_entry(g);
+        return fail_cuda(e, "cudaGraphLaunch");
+    }
+    g_kernel_launches += g.launches;
+    g_graphs.push_front(std::move(g));
+    while (g_graphs.size() > kMaxGraphs) {
+        destroy_entry(g_graphs.back());
+        g_graphs.pop_back();
+    }
+    return UMI_OK;
+}
+
+// ------------------------------------------------------------ autotuner --
+__global__ void fill_noise_kernel(float *x, int64_t n, uint64_t seed)
+{
+    // Flux-like samples 1 + N(0, 1e-3) from a counter-based hash (SplitMix64)
+    // and Box-Muller; only used to time kernels.
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + 0x9e3779b97f4a7c15ull * (uint64_t)(i + 1);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        const float u1 = ((z >> 40) + 1) * (1.0f / 16777217.0f);
+        const float u2 = ((z & 0xffffffu)) * (1.0f / 16777216.0f);
+        x[i] = 1.0f + 1e-3f * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    }
+}
+
+static umi_status time_plan(const Plan &plan, const float *flux, float *trend, float *detr,
+                            int64_t n, int W, cudaStream_t stream, double *ms)
+{
+    umi_params p;
+    umi_default_params(&p);
+    std::vector<Curve> curves{make_curve(flux, trend, detr, n, W, p)};
+    BatchLayout lay;
+    lay.bands.resize(1);
+    lay.bands[0].plan = plan;
+    lay.bands[0].first_item = 0;
+    const int64_t T = plan.tile();
+    const int64_t tiles = (n + T - 1) / T;
+    for (int64_t k = 0; k < tiles; ++k) lay.items.push_back(Item{0, (int32_t)k});
+    lay.bands[0].n_items = (int32_t)tiles;
+    umi_status st = prepare_kernel(plan, false);
+    if (st != UMI_OK) return st;
+    const Scratch sc = scratch_layout(1, lay.items.size(), 1);
+    std::vector<char> host(sc.counter_off);
+    memcpy(host.data() + sc.curve_off, curves.data(), sizeof(Curve));
+    memcpy(host.data() + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
+    void *dev = nullptr;
+    UMI_CUDA(cudaMalloc(&dev, sc.bytes), "cudaMalloc");
+    UMI_CUDA(cudaMemcpy(dev, host.data(), sc.counter_off, cudaMemcpyHostToDevice), "cudaMemcpy");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    for (int rep = 0; rep < 4 && st == UMI_OK; ++rep) {
+        cudaEventRecord(e0, stream);
+        st = enqueue_bands(lay, (char *)dev, sc, stream, nullptr);
+        cudaEventRecord(e1, stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(UMI_ERR_CUDA, "autotune run failed");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) best = std::min(best, (double)t);  // first run warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dev);
+    *ms = best;
+    return st;
+}
+
+}  // namespace umi
+
+using namespace umi;
+
+// ================================================================== C ABI ==
+extern "C" {
+
+void umi_default_params(umi_params *p)
+{
+    if (!p) return;
+    p->alpha = 2.0f;
+    p->c = 5.0f;
+    p->iters = 5;
+    p->min_valid = -1;
+}
+
+int32_t umi_window_length(double cadence_days, double window_days)
+{
+    if (!(cadence_days > 0.0) || !(window_days > 0.0) || !std::isfinite(cadence_days) ||
+        !std::isfinite(window_days))
+        return -1;
+    const double ratio = window_days / cadence_days;
+    if (!(ratio <= 1e9)) return -1;
+    const long long w = std::llround(ratio);
+    return (int32_t)(w | 1LL);
+}
+
+int32_t umi_max_window(void) { return kMaxWindow; }
+
+const char *umi_last_error(void) { return t_error.c_str(); }
+
+const char *umi_version(void) { return "umi-gb300 0.1.0 (sm_103a)"; }
+
+umi_status umi_detrend(const float *flux_d, int64_t n, int32_t W, const umi_params *params,
+                       float *trend_d, float *detr_d, void *stream)
+{
+    umi_status st = detrend_single(flux_d, n, W, params, trend_d, detr_d, nullptr,
+                                   (cudaStream_t)stream);
+    if (st == UMI_OK && n > 0) g_kernel_launches += 1;
+    return st;
+}
+
+umi_status umi_detrend_diag(const float *flux_d, int64_t n, int32_t W, const umi_params *params,
+                            float *trend_d, float *detr_d, float *median_d, int32_t *nvalid_d,
+                            int32_t *nplus_d, float *scale_d, void *stream)
+{
+    Diag d{median_d, nvalid_d, nplus_d, scale_d};
+    umi_status st = detrend_single(flux_d, n, W, params, trend_d, detr_d, &d, (cudaStream_t)stream);
+    if (st == UMI_OK && n > 0) g_kernel_launches += 1;
+    return st;
+}
+
+umi_status umi_detrend_batched(const float *flux_d, const int64_t *offsets_h, const int32_t *W_h,
+                               int32_t B, const umi_params *params, float *trend_d, float *detr_d,
+                               void *stream)
+{
+    return batched_impl(flux_d, offsets_h, W_h, B, params, trend_d, detr_d, (cudaStream_t)stream,
+                        true);
+}
+
+umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_h,
+                                    const int32_t *W_h, int32_t B, const umi_params *params,
+                                    float *trend_h, float *detr_h, void *stream)
+{
+    clear_error();
+    if (B < 0 || (B > 0 && (!offsets_h || !W_h))) return fail(UMI_ERR_INVALID_ARG, "bad batch");
+    if (B == 0) return UMI_OK;
+    const int64_t total = offsets_h[B];
+    if (total < 0) return fail(UMI_ERR_INVALID_ARG, "bad offsets");
+    if (total == 0)
+        return batched_impl(nullptr, offsets_h, W_h, B, params, nullptr, nullptr,
+                            (cudaStream_t)stream, false);
+    if (!flux_h || !trend_h || !detr_h) return fail(UMI_ERR_INVALID_ARG, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(float) * (size_t)total;
+    float *dev = nullptr;
+    UMI_CUDA(cudaMallocAsync((void **)&dev, 3 * bytes, s), "cudaMallocAsync");
+    umi_status st = UMI_OK;
+    cudaError_t e = cudaMemcpyAsync(dev, flux_h, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) st = fail_cuda(e, "cudaMemcpyAsync H2D");
+    if (st == UMI_OK) {
+        // The graph cache is keyed by device pointers, which change per call here.
+        st = batched_impl(dev, offsets_h, W_h, B, params, dev + total, dev + 2 * total, s, false);
+    }
+    if (st == UMI_OK) {
+        e = cudaMemcpyAsync(trend_h, dev + total, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(detr_h, dev + 2 * total, bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = fail_cuda(e, "cudaMemcpyAsync D2H");
+    }
+    cudaFreeAsync(dev, s);
+    e = cudaStreamSynchronize(s);
+    if (st == UMI_OK && e != cudaSuccess) st = fail_cuda(e, "cudaStreamSynchronize");
+    return st;
+}
+
+umi_status umi_get_plan(int32_t W, int64_t positions, umi_plan *out)
+{
+    clear_error();
+    if (!out) return fail(UMI_ERR_INVALID_ARG, "null plan");
+    Plan p;
+    umi_status st = make_plan(W, positions, &p);
+    if (st != UMI_OK) return st;
+    out->lanes = p.G;
+    out->slots = p.R;
+    out->chain = p.chain;
+    out->threads = p.threads;
+    out->variant = p.variant;
+    return UMI_OK;
+}
+
+umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *best_out,
+                        double *best_ms)
+{
+    clear_error();
+    if (W < 1 || (W % 2) == 0 || W > kMaxWindow) return fail(UMI_ERR_INVALID_ARG, "bad W");
+    if (positions < 1 || positions > (int64_t)1 << 31) return fail(UMI_ERR_INVALID_ARG, "bad positions");
+    cudaStream_t s = (cudaStream_t)stream;
+    float *buf = nullptr;
+    UMI_CUDA(cudaMalloc((void **)&buf, 3 * sizeof(float) * (size_t)positions), "cudaMalloc");
+    fill_noise_kernel<<<1024, 256, 0, s>>>(buf, positions, 0x5eedull + (uint64_t)W);
+    int nv = 0;
+    const Variant *t = variant_table(&nv);
+    Plan best;
+    double bms = 1e30;
+    umi_status st = UMI_OK;
+    int eligible = 0;
+    for (int v = 0; v < nv && st == UMI_OK; ++v) {
+        const int S = t[v].G * t[v].R;
+        if (S < W) continue;
+        if (eligible >= 3) break;  // the three smallest capacities that fit
+        ++eligible;
+        const int G = t[v].G;
+        for (int threads : {128, 256}) {
+            if (threads < G) continue;
+            for (int mult : {1, 3, 5, 9}) {
+                Plan p;
+                p.variant = v;
+                p.G = G;
+                p.R = t[v].R;
+                p.threads = threads;
+                p.chain = (G >= 32) ? 16 * mult : round_chain(G, G * mult * (G >= 8 ? 1 : 4));
+                if (!legal_chain(G, p.chain)) continue;
+                if (p.smem_bytes() > device_info(current_device()).smem_optin) continue;
+                double ms = 0;
+                st = time_plan(p, buf, buf + positions, buf + 2 * positions, positions, W, s, &ms);
+                if (st != UMI_OK) break;
+                if (ms < bms) {
+                    bms = ms;
+                    best = p;
+                }
+            }
+        }
+    }
+    cudaFree(buf);
+    if (st != UMI_OK) return st;
+    if (best.variant < 0) return fail(UMI_ERR_INVALID_ARG, "no eligible variant");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[W] = best;
+    }
+    if (best_out) {
+        best_out->lanes = best.G;
+        best_out->slots = best.R;
+        best_out->chain = best.chain;
+        best_out->threads = best.threads;
+        best_out->variant = best.variant;
+    }
+    if (best_ms) *best_ms = bms;
+    return UMI_OK;
+}
+
+umi_status umi_save_tuning(const char *path)
+{
+    clear_error();
+    if (!path) return fail(UMI_ERR_INVALID_ARG, "null path");
+    std::ofstream f(path);
+    if (!f) return fail(UMI_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    const std::string gpu = device_info(current_device()).name;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    f << "# umi tuning table: gpu|W|G|R|chain|threads\n";
+    for (auto &kv : g_tuned)
+        f << gpu << "|" << kv.first << "|" << kv.second.G << "|" << kv.second.R << "|"
+          << kv.second.chain << "|" << kv.second.threads << "\n";
+    return UMI_OK;
+}
+
+umi_status umi_load_tuning(const char *path)
+{
+    clear_error();
+    if (!path) return fail(UMI_ERR_INVALID_ARG, "null path");
+    std::ifstream f(path);
+    if (!f) return fail(UMI_ERR_INVALID_ARG, std::string("cannot read ") + path);
+    const std::string gpu = device_info(current_device()).name;
+    int nv = 0;
+    const Variant *t = variant_table(&nv);
+    std::string line;
+    std::map<int, Plan> loaded;
+    while (std::getline(f, line)) {
+        if (line.empty() || line[0] == '#') continue;
+        std::vector<std::string> parts;
+        std::stringstream ss(line);
+        std::string tok;
+        while (std::getline(ss, tok, '|')) parts.push_back(tok);
+        if (parts.size() != 6 || parts[0] != gpu) continue;
+        Plan p;
+        const int W = std::atoi(parts[1].c_str());
+        p.G = std::atoi(parts[2].c_str());
+        p.R = std::atoi(parts[3].c_str());
+        p.chain = std::atoi(parts[4].c_str());
+        p.threads = std::atoi(parts[5].c_str());
+        for (int v = 0; v < nv; ++v)
+            if (t[v].G == p.G && t[v].R == p.R) p.variant = v;
+        if (p.variant < 0 || W < 1 || (W % 2) == 0 || W > kMaxWindow || p.G * p.R < W ||
+            !legal_chain(p.G, p.chain) || p.threads < p.G || p.threads > 256 || p.threads % 32)
+            return fail(UMI_ERR_INVALID_ARG, "bad tuning line: " + line);
+        loaded[W] = p;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : loaded) g_tuned[kv.first] = kv.second;
+    return UMI_OK;
+}
+
+void umi_clear_tuning(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+}
+
+void umi_set_graph_cache(int enabled)
+{
+    g_graph_enabled.store(enabled ? 1 : 0);
+    if (!enabled) {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (auto &g : g_graphs) destroy_entry(g);
+        g_graphs.clear();
+    }
+}
+
+// Number of kernels this library has launched in the process (for reports).
+long long umi_kernel_launch_count(void) { return g_kernel_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// umi_internal.h -- shared host-side pieces of libumi (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/umi.h"
+#include "umi_kernel.cuh"
+#include "umi_variants.h"
+
+namespace umi {
+
+// Records a message for umi_last_error() and returns the status.
+umi_status fail(umi_status st, const std::string &msg);
+umi_status fail_cuda(cudaError_t err, const char *what);
+void clear_error();
+
+struct DeviceInfo {
+    int device = -1;
+    int sms = 0;
+    size_t smem_optin = 0;
+    std::string name;
+};
+const DeviceInfo &device_info(int device);
+int current_device();
+
+// A launch plan for one window band.
+struct Plan {
+    int variant = -1;
+    int G = 0, R = 0;
+    int chain = 0;    // positions per group
+    int threads = 0;  // per CTA
+    int tile() const { return (threads / G) * chain; }
+    size_t smem_bytes() const { return sizeof(float) * (size_t)(tile() + G * R - 1); }
+};
+
+bool legal_chain(int G, int chain);
+// Plan for a window length; `positions` sizes the chain when the work is small.
+umi_status make_plan(int W, int64_t positions, Plan *plan);
+umi_status check_params(const umi_params *p, umi_params *out);
+int resolve_min_valid(int W, int min_valid);
+umi_status prepare_kernel(const Plan &plan, bool diag);
+// Persistent grid size for a plan on the current device.
+int persistent_grid(const Plan &plan, bool diag);
+
+// One batched launch over an explicit curve table (used by the CSR entry
+// point and by the server).  `curves` are host descriptors with device data
+// pointers; device scratch is taken with cudaMallocAsync on `stream`.
+// `launches` (may be null) receives the number of kernels launched.
+umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream,
+                              int *launches);
+
+// Work-item list and per-variant launch layout for a curve table.
+struct BatchLayout {
+    struct Band {
+        Plan plan;
+        int32_t first_item = 0;
+        int32_t n_items = 0;
+    };
+    std::vector<Band> bands;
+    std::vector<Item> items;
+};
+umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout);
+
+}  // namespace umi

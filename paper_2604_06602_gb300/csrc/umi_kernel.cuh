@@ -1,0 +1,436 @@
+// umi_kernel.cuh -- sm_103a kernel for the UMI sliding-window robust trend.
+//
+// Method (paper Section 2): per output position, over the W-sample window
+// with missing samples dropped: Phase 1 exact median (Section 2.1), Phase 2
+// upper-RMS scale s = 0.6745 sqrt(mean_{x > m} (x - m)^2) (Eq. 1), Phase 3
+// `iters` asymmetric bisquare reweighting steps (Eqs. 2-4), trend = mu,
+// detrended flux = x / mu.
+//
+// GPU design (not the paper's one-thread-per-window kernel, Section 2.6):
+//  * A CTA owns a tile of T consecutive positions of one curve and stages the
+//    T + S - 1 samples its windows touch into shared memory once; missing
+//    samples (non-finite, or outside the curve) become kGap.
+//  * A "group" of G lanes (G = 1..32, a power of two) evaluates one window at a
+//    time, each lane holding R window slots in registers (S = G*R >= W slots;
+//    slots past W hold kGap).  The 32/G groups of a warp run in lock step on
+//    neighbouring chains; every block that shuffles is entered warp-uniformly.
+//  * Each group walks a chain of P consecutive positions.  At the chain start
+//    (or after an empty window) the median comes from an exact bitwise radix
+//    select on order-preserving integer keys.  Afterwards the group keeps the
+//    counts L = #{x < m}, E = #{x == m}, G+ = #{x > m} of the current window
+//    and updates them in O(1) per step from the sample that leaves and the one
+//    that enters.  One step moves the median's rank by at most one, so the new
+//    median is m itself, the largest sample below m, or the smallest above m;
+//    the last two take one pass over the registers.  Every median is the exact
+//    order statistic of rank floor((n_valid - 1)/2).
+//  * Eq. 1 is one pass over the registers, G+ comes from the counts.
+//  * Phase 3 keeps y = x - m in registers and runs the fixed number of steps
+//    on mu = m + delta: per slot r = y - delta, q = r*a + |r|*b (a, b fold the
+//    asymmetry of Eq. 2 and 1/(c s)), z = sat(1 - q^2), w = z^2 (Eq. 3), and
+//    the centred sums sum(w), sum(w r) give delta += sum(w r)/sum(w) (Eq. 4).
+//    A kGap slot has |q| >= 1 (or q overflows / is NaN), so sat() makes its
+//    weight exactly 0 without a mask.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace umi {
+
+// Missing-sample marker inside the tile.  Finite, below every admissible
+// sample (|x| < 2^60), and so far below that its standardised residual never
+// reaches the bisquare support.
+constexpr float kGap = -0x1p100f;
+constexpr float kGapLimit = -0x1p99f;  // x > kGapLimit  <=>  a real sample
+constexpr float kScaleFactor = 0.6745f;  // Section 2.2, as printed
+
+struct Curve {
+    const float *flux;
+    float *trend;
+    float *detr;
+    int64_t n;
+    int32_t W;
+    int32_t min_valid;  // resolved, >= 0
+    float alpha;
+    float c;
+    int32_t iters;
+    int32_t reserved;
+};
+
+struct Diag {
+    float *median;
+    int32_t *nvalid;
+    int32_t *nplus;
+    float *scale;
+};
+
+struct Item {
+    int32_t curve;  // index into the curve table
+    int32_t tile;   // tile index within the curve; first position = tile * T
+};
+
+struct LaunchArgs {
+    const Curve *curves;  // device curve table, or nullptr to use `single`
+    Curve single;
+    const Item *items;    // device item list, or nullptr: item i = {0, i}
+    int32_t n_items;
+    int32_t chain;        // P: consecutive positions per group
+    int32_t *queue;       // persistent work counter, or nullptr: one item per CTA
+    Diag diag;
+};
+
+// ---- group-wide reductions over G aligned lanes --------------------------
+template <int G>
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ int group_sum_int(int v)
+{
+    if constexpr (G == 32) {
+        return (int)__reduce_add_sync(0xffffffffu, (unsigned)v);
+    } else {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ float group_max(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_umin(unsigned v)
+{
+    if constexpr (G == 32) {
+        return __reduce_min_sync(0xffffffffu, v);
+    } else {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_umax(unsigned v)
+{
+    if constexpr (G == 32) {
+        return __reduce_max_sync(0xffffffffu, v);
+    } else {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
+}
+
+// Order-preserving map from non-NaN floats to unsigned keys (-0 sorts just
+// below +0; the counts that follow compare floats, where they are equal).
+__device__ __forceinline__ unsigned float_key(float f)
+{
+    unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_float(unsigned k)
+{
+    unsigned b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(b);
+}
+
+// Load the window of tile position q into registers: slot s = glane + G*i
+// holds tile[q + s] for s < W, kGap past W.  `tail_only` (uniform) says that
+// G*(R-1) < W, so only the last register row can hold slots past W; the
+// general path re-derives each row's limit from an opaque register so the
+// compiler does not keep R loop-invariant predicates alive across the chain.
+template <int G, int R>
+__device__ __forceinline__ void load_window(float (&x)[R], const float *tile, int q, int glane,
+                                            int W, bool tail_only)
+{
+    const float *base = tile + q + glane;
+    if (tail_only) {
+#pragma unroll
+        for (int i = 0; i < R - 1; ++i) x[i] = base[G * i];
+        const float v = base[G * (R - 1)];
+        x[R - 1] = (glane + G * (R - 1) < W) ? v : kGap;
+    } else {
+        int lim = W - glane;  // slot row i is valid for this lane iff G*i < lim
+        asm volatile("" : "+r"(lim));
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const float v = base[G * i];
+            x[i] = (G * i < lim) ? v : kGap;
+        }
+    }
+}
+
+// Per-group median state carried along a chain.
+struct MedianState {
+    float m;   // current median (valid when `have`)
+    int L;     // valid samples < m
+    int E;     // samples == m
+    int Gp;    // samples > m
+    int nv;    // valid samples in the window
+    bool have;
+};
+
+template <int G, int R, bool DIAG>
+__device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, const float *tile,
+                                              int64_t t0, int q0, int P, int glane)
+{
+    constexpr int S = G * R;
+    const int W = cv.W;
+    const int h = (W - 1) >> 1;
+    const float alpha = cv.alpha;
+    const float cst = cv.c;
+    const int iters = cv.iters;
+    const bool tail_only = G * (R - 1) < W;
+    float x[R];
+    MedianState st;
+    st.m = 0.f;
+    st.L = st.E = st.Gp = 0;
+    st.nv = 0;
+    st.have = false;
+
+#pragma unroll 1
+    for (int t = 0; t < P; ++t) {
+        const int q = q0 + t;
+        const int64_t p = t0 + q;
+
+        // ---- slide: one sample leaves, one enters --------------------------
+        if (t > 0) {
+            const float out = tile[q - 1];
+            const float in = tile[q + W - 1];
+            const bool ov = out > kGapLimit;
+            const bool iv = in > kGapLimit;
+            st.nv += (int)iv - (int)ov;
+            if (st.have) {
+                if (ov) {
+                    if (out < st.m) --st.L;
+                    else if (out == st.m) --st.E;
+                    else --st.Gp;
+                }
+                if (iv) {
+                    if (in < st.m) ++st.L;
+                    else if (in == st.m) ++st.E;
+                    else ++st.Gp;
+                }
+            }
+        }
+
+        load_window<G, R>(x, tile, q, glane, W, tail_only);
+
+        if (t == 0) {
+            int c = 0;
+#pragma unroll
+            for (int i = 0; i < R; ++i) c += (x[i] > kGapLimit) ? 1 : 0;
+            st.nv = group_sum_int<G>(c);
+        }
+        if (st.nv == 0) st.have = false;
+        const int k = (st.nv - 1) >> 1;  // rank of the lower median among valid samples
+        const bool need_full = (st.nv >= 1) && !st.have;
+        // 0 = median unchanged, +1 = moves to the largest sample below m,
+        // -1 = moves to the smallest sample above m.
+        int move = 0;
+        if (st.have) {
+            if (k < st.L) move = 1;
+            else if (k >= st.L + st.E) move = -1;
+        }
+
+        // ---- exact radix select (chain start / restart) --------------------
+        if (__any_sync(0xffffffffu, need_full)) {
+            // Bitwise binary search for the key of rank `target` among the S
+            // slots.  It reads the window from shared memory (it runs once per
+            // chain), which keeps the register arrays free for the hot loops.
+            const float *wb = tile + q + glane;
+            int lim = W - glane;
+            asm volatile("" : "+r"(lim));
+            unsigned lo = 0xffffffffu, hi = 0u;
+#pragma unroll 4
+            for (int i = 0; i < R; ++i) {
+                const float v = wb[G * i];
+                const bool valid = (G * i < lim) && (v > kGapLimit);
+                const unsigned kk = float_key(v);
+                lo = valid ? min(lo, kk) : lo;
+                hi = valid ? max(hi, kk) : hi;
+            }
+            lo = group_umin<G>(lo);
+            hi = group_umax<G>(hi);
+            const unsigned diff = lo ^ hi;
+            const int nbits = diff ? 32 - __clz((int)diff) : 0;
+            unsigned res = (nbits >= 32) ? 0u : (lo & ~((1u << nbits) - 1u));
+            const int target = (S - st.nv) + k;  // rank among all S slots
+            const int nb = (int)__reduce_max_sync(0xffffffffu, (unsigned)(need_full ? nbits : 0));
+#pragma unroll 1
+            for (int b = nb - 1; b >= 0; --b) {
+                const unsigned cand = res | (1u << b);
+                int c = 0;
+#pragma unroll 4
+                for (int i = 0; i < R; ++i) {
+                    const float v = (G * i < lim) ? wb[G * i] : kGap;
+                    c += (float_key(v) < cand) ? 1 : 0;
+                }
+                c = group_sum_int<G>(c);
+                if (c <= target) res = cand;
+            }
+            const float mf = key_float(res);
+            int cl = 0, ce = 0;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                cl += (x[i] < mf) ? 1 : 0;
+                ce += (x[i] == mf) ? 1 : 0;
+            }
+            cl = group_sum_int<G>(cl);
+            ce = group_sum_int<G>(ce);
+            if (need_full) {
+                st.m = mf;
+                st.L = cl - (S - st.nv);
+                st.E = ce;
+                st.Gp = st.nv - st.L - st.E;
+                st.have = true;
+            }
+        }
+
+        // ---- one-rank move of the median -----------------------------------
+        if (__any_sync(0xffffffffu, move != 0)) {
+            const float sg = (move < 0) ? -1.f : 1.f;
+            const float sm = sg * st.m;
+            float best = -INFINITY;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const float y = sg * x[i];
+                best = (y < sm) ? fmaxf(best, y) : best;
+            }
+            best = group_max<G>(best);
+            const float cand = sg * best;
+            int e = 0;
+#pragma unroll
+            for (int i = 0; i < R; ++i) e += (x[i] == cand) ? 1 : 0;
+            e = group_sum_int<G>(e);
+            if (move > 0) {
+                st.Gp += st.E;
+                st.L -= e;
+                st.E = e;
+                st.m = cand;
+            } else if (move < 0) {
+                st.L += st.E;
+                st.Gp -= e;
+                st.E = e;
+                st.m = cand;
+            }
+        }
+
+        // ---- Phases 2 and 3 -------------------------------------------------
+        const float centre = tile[q + h];
+        const bool produce = (p < cv.n) && (st.nv >= 1) && (st.nv >= cv.min_valid) &&
+                             (centre > kGapLimit);
+        float mu = st.m;
+        float s = 0.f;
+        if (__any_sync(0xffffffffu, produce)) {
+            const float m = st.m;
+            float s2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                x[i] = x[i] - m;  // y = x - m, exact sign
+                const float yp = fmaxf(x[i], 0.f);
+                s2 = fmaf(yp, yp, s2);
+            }
+            s2 = group_sum<G>(s2);
+            s = (st.Gp > 0) ? kScaleFactor * sqrtf(s2 / (float)st.Gp) : 0.f;
+            const bool iterate = produce && (s > 0.f);
+            if (__any_sync(0xffffffffu, iterate)) {
+                const float inv = 1.f / (cst * s);
+                const float ca = 0.5f * (1.f + alpha) * inv;  // q = r*ca + |r|*cb:
+                const float cb = 0.5f * (1.f - alpha) * inv;  // r/(cs) for r >= 0, alpha r/(cs) below
+                float delta = 0.f;
+#pragma unroll 1
+                for (int it = 0; it < iters; ++it) {
+                    float sw = 0.f, swr = 0.f;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        const float r = x[i] - delta;
+                        const float qv = fmaf(fabsf(r), cb, r * ca);
+                        const float z = __saturatef(fmaf(-qv, qv, 1.f));
+                        const float w = z * z;
+                        sw += w;
+                        swr = fmaf(w, r, swr);
+                    }
+                    sw = group_sum<G>(sw);
+                    swr = group_sum<G>(swr);
+                    if (sw > 0.f) delta += swr / sw;
+                }
+                if (iterate) mu = m + delta;
+            }
+        }
+
+        if (glane == 0 && p < cv.n) {
+            const float nanv = __int_as_float(0x7fc00000);
+            cv.trend[p] = produce ? mu : nanv;
+            cv.detr[p] = produce ? __fdiv_rn(centre, mu) : nanv;
+            if constexpr (DIAG) {
+                if (dg.median) dg.median[p] = (st.nv >= 1) ? st.m : nanv;
+                if (dg.nvalid) dg.nvalid[p] = st.nv;
+                if (dg.nplus) dg.nplus[p] = (st.nv >= 1) ? st.Gp : 0;
+                if (dg.scale) dg.scale[p] = produce ? s : nanv;
+            }
+        }
+    }
+}
+
+// One CTA per work item (queue == nullptr) or a persistent CTA pulling items
+// from the queue counter.  Dynamic shared memory: (T + S - 1) floats,
+// T = (blockDim.x / G) * chain.
+template <int G, int R, bool DIAG>
+__global__ void __launch_bounds__(256) umi_tile_kernel(LaunchArgs a)
+{
+    extern __shared__ float tile[];
+    __shared__ int s_item;
+    constexpr int S = G * R;
+    const int glane = threadIdx.x & (G - 1);
+    const int group = threadIdx.x / G;
+    const int n_groups = blockDim.x / G;
+    const int P = a.chain;
+    const int T = n_groups * P;
+    const int tile_len = T + S - 1;
+
+    int next = blockIdx.x;
+    for (;;) {
+        int item;
+        if (a.queue) {
+            if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+            __syncthreads();
+            item = s_item;
+        } else {
+            item = next;
+        }
+        if (item >= a.n_items) break;
+        const Item wi = a.items ? a.items[item] : Item{0, item};
+        const Curve cv = a.curves ? a.curves[wi.curve] : a.single;
+        const int64_t t0 = (int64_t)wi.tile * T;
+        const int h = (cv.W - 1) >> 1;
+
+        for (int k = threadIdx.x; k < tile_len; k += blockDim.x) {
+            const int64_t idx = t0 - h + k;
+            float v = kGap;
+            if (idx >= 0 && idx < cv.n) {
+                const float f = __ldg(cv.flux + idx);
+                if (isfinite(f)) v = f;
+            }
+            tile[k] = v;
+        }
+        __syncthreads();
+        process_chain<G, R, DIAG>(cv, a.diag, tile, t0, group * P, P, glane);
+        __syncthreads();
+        if (!a.queue) break;
+    }
+}
+
+}  // namespace umi

@@ -1,0 +1,81 @@
+"""Shared comparison helpers for the parity tests."""
+import numpy as np
+
+# The trend tolerance is 1e-5 relative per sample.  For curves centred near
+# zero (synthetic edge cases, not flux) a relative bound is meaningless, so
+# those use 1e-5 of max(|trend|, c * s): the FP32 path's error scales with
+# the window's spread (c s) as well as with the level.
+TREND_RTOL = 1e-5
+
+
+def compare_diag(got, ref, c=5.0, scale_aware=False, what=""):
+    """got: dict of numpy arrays from the GPU diag path; ref: oracle dict."""
+    n = ref["trend"].size
+    assert got["trend"].size == n
+    # Counts are integers: bit-exact.
+    np.testing.assert_array_equal(got["nvalid"], ref["nvalid"], err_msg=what + " nvalid")
+    np.testing.assert_array_equal(got["nplus"], ref["nplus"], err_msg=what + " nplus")
+    # Median: an FP32 order statistic of the inputs, compared as a value.
+    mref = ref["median"]
+    mgot = got["median"].astype(np.float64)
+    np.testing.assert_array_equal(np.isnan(mgot), np.isnan(mref), err_msg=what + " median NaN")
+    ok = ~np.isnan(mref)
+    bad = np.nonzero(mgot[ok] != mref[ok])[0]
+    assert bad.size == 0, "%s median differs at %s: %s vs %s" % (
+        what, np.nonzero(ok)[0][bad[:5]], mgot[ok][bad[:5]], mref[ok][bad[:5]])
+    compare_trend(got["trend"], ref["trend"], ref.get("scale"), c, scale_aware, what)
+    compare_detr(got["detr"], ref["detr"], what)
+
+
+def compare_trend(tgot, tref, sref=None, c=5.0, scale_aware=False, what=""):
+    tgot = np.asarray(tgot, np.float64)
+    np.testing.assert_array_equal(np.isnan(tgot), np.isnan(tref), err_msg=what + " trend NaN pattern")
+    ok = ~np.isnan(tref)
+    if not ok.any():
+        return
+    bound = np.abs(tref[ok])
+    if scale_aware and sref is not None:
+        bound = np.maximum(bound, c * np.nan_to_num(sref[ok]))
+    err = np.abs(tgot[ok] - tref[ok])
+    lim = TREND_RTOL * bound
+    worst = np.argmax(err - lim)
+    assert np.all(err <= lim), "%s trend off at %d: got %r ref %r (err %g, lim %g)" % (
+        what, np.nonzero(ok)[0][worst], tgot[ok][worst], tref[ok][worst], err[worst], lim[worst])
+
+
+def compare_detr(dgot, dref, what=""):
+    dgot = np.asarray(dgot, np.float64)
+    np.testing.assert_array_equal(np.isnan(dgot), np.isnan(dref), err_msg=what + " detr NaN pattern")
+    ok = ~np.isnan(dref) & np.isfinite(dref)
+    err = np.abs(dgot[ok] - dref[ok])
+    lim = TREND_RTOL * np.abs(dref[ok]) + 1e-30
+    assert np.all(err <= lim), "%s detr off by %g" % (what, float((err / lim).max()))
+
+
+def depth_recovery_errors(detr, batch, idx=None):
+    """Median-free per-curve depth recovery error (percent).
+
+    Reading of the paper's metric (median of per-star absolute percentage
+    errors, Section 3.2): recovered depth = median of detrended flux over the
+    out-of-transit samples within one transit duration of each transit, minus
+    the mean detrended flux inside transits; injected depth = mean injected
+    profile over the same in-transit samples."""
+    idx = range(batch.B) if idx is None else idx
+    errs = []
+    for b in idx:
+        s = slice(batch.offsets[b], batch.offsets[b + 1])
+        d = np.asarray(detr[s], np.float64)
+        prof = batch.transit[s].astype(np.float64)
+        n = d.size
+        cad = batch.cadence[b]
+        t = np.arange(n) * cad
+        per, ep, dur = batch.period_d[b], batch.epoch_d[b], batch.duration_d[b]
+        phase = np.abs(np.mod(t - ep + 0.5 * per, per) - 0.5 * per)
+        intr = (prof > 0) & np.isfinite(d)
+        near = (phase > 0.5 * dur) & (phase < 1.5 * dur) & np.isfinite(d)
+        if intr.sum() < 3 or near.sum() < 3:
+            continue
+        d_rec = np.median(d[near]) - np.mean(d[intr])
+        d_inj = np.mean(prof[intr])
+        errs.append(abs(d_rec - d_inj) / d_inj * 100.0)
+    return np.array(errs)

@@ -1,0 +1,96 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every function include/umi.h declares, and validates arguments on the host
+(no kernel is launched here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_06602_gb300 import build as libbuild
+from paper_2604_06602_gb300 import umi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return umi.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "umi.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(umi_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_matches_binding_list():
+    assert declared_functions() == sorted(umi.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_window_length_matches_oracle(lib):
+    for dt_min in list(np.linspace(0.2, 60.0, 997)) + [2.0, 29.4, 30.0, 20.0 / 60.0]:
+        dt = dt_min / 1440.0
+        for wd in (0.25, 0.5, 1.5):
+            assert umi.window_length(dt, wd) == oracle.window_length(dt, wd)
+    assert umi.window_length(0.0) == -1
+    assert umi.window_length(float("inf")) == -1
+
+
+def test_default_params(lib):
+    p = umi.default_params()
+    assert (p.alpha, p.c, p.iters, p.min_valid) == (2.0, 5.0, 5, -1)
+    assert umi.max_window() >= 2161
+
+
+def test_host_validation_without_gpu(lib):
+    p = umi.default_params()
+    buf = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    bad = [
+        (buf, 100, 4, p),   # even window
+        (buf, 100, 0, p),   # zero window
+        (buf, -1, 3, p),    # negative length
+        (buf, 100, umi.max_window() + 2, p),
+    ]
+    for flux, n, W, pp in bad:
+        st = lib.umi_detrend(flux, n, W, ctypes.byref(pp), buf, buf, None)
+        assert st == umi.UMI_ERR_INVALID_ARG
+        assert lib.umi_last_error()
+    for field, val in (("alpha", 0.0), ("c", -1.0), ("iters", -2), ("min_valid", -5)):
+        q = umi.default_params()
+        setattr(q, field, val)
+        assert lib.umi_detrend(buf, 10, 3, ctypes.byref(q), buf, buf, None) == umi.UMI_ERR_INVALID_ARG
+    # n == 0 is a no-op, not an error.
+    assert lib.umi_detrend(None, 0, 3, None, None, None, None) == umi.UMI_OK
+    # Batched: bad offsets and windows are caught before any device work.
+    off = np.array([0, 5, 3], np.int64)
+    W = np.array([3, 3], np.int32)
+    st = lib.umi_detrend_batched(buf, off.ctypes.data_as(ctypes.c_void_p),
+                                 W.ctypes.data_as(ctypes.c_void_p), 2, None, buf, buf, None)
+    assert st == umi.UMI_ERR_INVALID_ARG
+    off = np.array([1, 5, 8], np.int64)
+    st = lib.umi_detrend_batched(buf, off.ctypes.data_as(ctypes.c_void_p),
+                                 W.ctypes.data_as(ctypes.c_void_p), 2, None, buf, buf, None)
+    assert st == umi.UMI_ERR_INVALID_ARG
+    off = np.array([0, 5, 8], np.int64)
+    W = np.array([3, 6], np.int32)
+    st = lib.umi_detrend_batched(buf, off.ctypes.data_as(ctypes.c_void_p),
+                                 W.ctypes.data_as(ctypes.c_void_p), 2, None, buf, buf, None)
+    assert st == umi.UMI_ERR_INVALID_ARG
+
+
+def test_version(lib):
+    assert "sm_103a" in umi.version()
+
+
+def test_built_for_sm103a_only():
+    assert libbuild.ARCH_FLAGS == ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,280 @@
+"""GPU parity: libumi (through the C ABI) against the FP64 oracle.
+
+Bar: valid counts, above-median counts and medians bit-exact; trend within
+1e-5 relative per sample (scale-aware only for synthetic curves centred near
+zero, see helpers.py); NaN outputs at identical positions; the depth-recovery
+aggregate within 0.1 percentage points of the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_06602_gb300 import synth
+from tests.helpers import compare_diag, compare_trend, compare_detr, depth_recovery_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def umi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_06602_gb300 import umi as u
+    u.load(build_if_missing=True)
+    return u
+
+
+def run_diag(umi, x, W, p=None):
+    xd = torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    out = umi.detrend_diag(xd, W, p)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def oracle_params(p):
+    if p is None:
+        return {}
+    return dict(alpha=p.alpha, c=p.c, iters=p.iters, min_valid=p.min_valid)
+
+
+def tile_of(umi, W):
+    pl = umi.get_plan(W, -1)
+    return pl["threads"] // pl["lanes"] * pl["chain"]
+
+
+WINDOWS = [1, 3, 7, 25, 33, 129, 361, 369, 769, 1537, 2161, 4095]
+
+
+@pytest.mark.parametrize("W", WINDOWS)
+def test_lengths_around_window_and_tiles(umi, W):
+    T = tile_of(umi, W)
+    for n in sorted({1, 2, max(1, W - 1), W, W + 1, 3 * T + 5}):
+        x = synth.random_curve(1000 + n, n, level=1.0, sigma=1e-3)
+        compare_diag(run_diag(umi, x, W), oracle.detrend(x, W), what="W=%d n=%d" % (W, n))
+
+
+@pytest.mark.parametrize("W", [3, 25, 361, 2161])
+def test_gaps_ties_and_edges(umi, W):
+    n = 3 * tile_of(umi, W) + 17
+    cases = {
+        "nan_runs": synth.random_curve(1, n, nan_runs=6, run_len=(1, 2 * W)),
+        "isolated_nan": synth.random_curve(2, n, nan_frac=0.2),
+        "ties": synth.random_curve(3, n, quantum=5e-4),
+        "heavy_ties": synth.random_curve(4, n, quantum=3e-3, nan_frac=0.05),
+        "edge_gaps": synth.random_curve(5, n),
+        "inf_and_nan": synth.random_curve(6, n, nan_frac=0.05),
+    }
+    x = cases["edge_gaps"]
+    x[: W // 2 + 3] = np.nan
+    x[-(W // 3 + 2):] = np.nan
+    y = cases["inf_and_nan"]
+    y[::97] = np.inf
+    y[5::89] = -np.inf
+    for name, x in cases.items():
+        compare_diag(run_diag(umi, x, W), oracle.detrend(x, W), what="%s W=%d" % (name, W))
+
+
+@pytest.mark.parametrize("W", [3, 25, 361, 2161])
+def test_all_missing_constant_and_sparse(umi, W):
+    n = 2 * tile_of(umi, W) + 3
+    x = np.full(n, np.nan, np.float32)
+    got = run_diag(umi, x, W)
+    assert np.all(np.isnan(got["trend"])) and np.all(got["nvalid"] == 0)
+    compare_diag(got, oracle.detrend(x, W), what="all-NaN")
+    x = np.full(n, 1.25, np.float32)
+    got = run_diag(umi, x, W)
+    assert np.all(got["trend"] == 1.25) and np.all(got["detr"] == 1.0)
+    # Constant runs separated by gaps, and isolated samples below min_valid.
+    x = synth.random_curve(9, n)
+    x[n // 4: n // 2] = 0.9995
+    x[n // 2: n // 2 + W] = np.nan
+    x[n // 2 + W // 2] = 1.0
+    compare_diag(run_diag(umi, x, W), oracle.detrend(x, W), what="runs W=%d" % W)
+    x = np.full(n, np.nan, np.float32)
+    x[:: max(2, W // 2)] = 1.0 + np.arange(x[:: max(2, W // 2)].size, dtype=np.float32) * 1e-4
+    compare_diag(run_diag(umi, x, W), oracle.detrend(x, W), what="sparse W=%d" % W)
+    compare_diag(run_diag(umi, x, W, umi.params(min_valid=0)), oracle.detrend(x, W, min_valid=0),
+                 what="sparse min_valid=0 W=%d" % W)
+
+
+@pytest.mark.parametrize("preset", [(2.0, 5.0), (3.0, 5.0), (1.0, 5.0), (10.0, 2.5), (0.5, 4.0)])
+def test_parameter_presets(umi, preset):
+    """Table 4 presets (and alpha < 1) on flux-like data with flares and dips."""
+    alpha, c = preset
+    b = synth.config1()
+    x = b.curve(0)[:6000].copy()
+    p = umi.params(alpha=alpha, c=c)
+    compare_diag(run_diag(umi, x, 361, p), oracle.detrend(x, 361, alpha=alpha, c=c),
+                 what="alpha=%g c=%g" % preset)
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2, 7])
+def test_iteration_counts(umi, iters):
+    x = synth.config1().curve(0)[:3000].copy()
+    p = umi.params(iters=iters)
+    compare_diag(run_diag(umi, x, 361, p), oracle.detrend(x, 361, iters=iters), what="iters=%d" % iters)
+
+
+def test_zero_centred_and_scaled(umi):
+    """Curves centred on zero and far from unit scale; the trend bound is
+    1e-5 of max(|trend|, c s) here."""
+    rng = np.random.default_rng(77)
+    for level, sigma in ((0.0, 1.0), (0.0, 1e-6), (1e4, 30.0), (-5.0, 0.1)):
+        x = (level + sigma * rng.standard_normal(3000)).astype(np.float32)
+        x[rng.uniform(size=x.size) < 0.03] = np.nan
+        compare_diag(run_diag(umi, x, 129), oracle.detrend(x, 129), scale_aware=True,
+                     what="level=%g sigma=%g" % (level, sigma))
+    x = rng.integers(-3, 4, 2000).astype(np.float32)   # integers: ties everywhere
+    compare_diag(run_diag(umi, x, 61), oracle.detrend(x, 61), scale_aware=True, what="integers")
+
+
+def test_config1_full_and_depth_recovery(umi):
+    b = synth.config1()
+    x = b.curve(0)
+    W = umi.window_length(b.cadence[0])
+    assert W == 361
+    got = run_diag(umi, x, W)
+    ref = oracle.detrend(x, W)
+    compare_diag(got, ref, what="config1")
+    e_gpu = depth_recovery_errors(got["detr"], b)
+    e_ref = depth_recovery_errors(ref["detr"], b)
+    assert e_gpu.size == 1 and abs(e_gpu[0] - e_ref[0]) < 0.1
+
+
+@pytest.fixture(scope="module")
+def config2(umi):
+    b = synth.config2()
+    W = np.array([umi.window_length(c) for c in b.cadence], np.int32)
+    assert np.all(W == 361)
+    flux = torch.from_numpy(b.flux).cuda()
+    tr, de = umi.detrend_batched(flux, b.offsets, W)
+    torch.cuda.synchronize()
+    return b, W, tr.cpu().numpy(), de.cpu().numpy()
+
+
+def test_config2_batched_full_curves_and_depth(umi, config2):
+    b, W, tr, de = config2
+    sub = np.arange(0, b.B, b.B // 48)[:48]
+    s = b.subset(sub)
+    rt, rd = oracle.detrend_batch(s.flux, s.offsets, W[sub])
+    gt = np.concatenate([tr[b.offsets[i]:b.offsets[i + 1]] for i in sub])
+    gd = np.concatenate([de[b.offsets[i]:b.offsets[i + 1]] for i in sub])
+    compare_trend(gt, rt, what="config2 subset")
+    compare_detr(gd, rd, what="config2 subset")
+    e_gpu = np.median(depth_recovery_errors(gd, s))
+    e_ref = np.median(depth_recovery_errors(rd, s))
+    assert abs(e_gpu - e_ref) < 0.1, (e_gpu, e_ref)
+
+
+def test_config2_batched_sampled_positions_all_curves(umi, config2):
+    b, W, tr, de = config2
+    rng = np.random.default_rng(5)
+    for i in range(b.B):
+        x = b.curve(i)
+        n = x.size
+        pos = np.unique(np.concatenate([[0, 1, 179, 180, 181, n // 2 - 361, n // 2 + 361, n - 2, n - 1],
+                                        rng.integers(0, n, 6)]))
+        pos = pos[(pos >= 0) & (pos < n)]
+        ref = oracle.detrend_positions(x, W[i], pos)
+        o = b.offsets[i]
+        compare_trend(tr[o + pos], ref["trend"], what="config2 curve %d" % i)
+        compare_detr(de[o + pos], ref["detr"], what="config2 curve %d" % i)
+
+
+def test_config3_uneven_batch(umi):
+    b = synth.config3(n_curves=96)
+    W = np.array([umi.window_length(c) for c in b.cadence], np.int32)
+    assert set(W.tolist()) == {25, 361}
+    flux = torch.from_numpy(b.flux).cuda()
+    tr, de = umi.detrend_batched(flux, b.offsets, W)
+    torch.cuda.synchronize()
+    tr, de = tr.cpu().numpy(), de.cpu().numpy()
+    rt, rd = oracle.detrend_batch(b.flux, b.offsets, W)
+    compare_trend(tr, rt, what="config3")
+    compare_detr(de, rd, what="config3")
+    # Batched output is bit-identical to one launch per curve.
+    for i in range(0, b.B, 7):
+        x = torch.from_numpy(b.curve(i).copy()).cuda()
+        t1, d1 = umi.detrend(x, int(W[i]))
+        torch.cuda.synchronize()
+        s = slice(b.offsets[i], b.offsets[i + 1])
+        assert np.array_equal(t1.cpu().numpy(), tr[s], equal_nan=True)
+        assert np.array_equal(d1.cpu().numpy(), de[s], equal_nan=True)
+
+
+def test_config4_large_window_sampled(umi):
+    b = synth.config4(n_curves=6)
+    W = np.array([umi.window_length(c) for c in b.cadence], np.int32)
+    assert np.all(W == 2161)
+    flux = torch.from_numpy(b.flux).cuda()
+    tr, de = umi.detrend_batched(flux, b.offsets, W)
+    torch.cuda.synchronize()
+    tr, de = tr.cpu().numpy(), de.cpu().numpy()
+    rng = np.random.default_rng(8)
+    for i in range(b.B):
+        x = b.curve(i)
+        n = x.size
+        g0 = int(np.argmax(np.isnan(x)))
+        pos = np.unique(np.concatenate([np.arange(0, 40), np.arange(n - 40, n),
+                                        np.arange(g0 - 1100, g0 + 20), rng.integers(0, n, 300)]))
+        ref = oracle.detrend_positions(x, 2161, pos)
+        o = b.offsets[i]
+        compare_trend(tr[o + pos], ref["trend"], what="config4 curve %d" % i)
+        compare_detr(de[o + pos], ref["detr"], what="config4 curve %d" % i)
+
+
+def test_batch_with_empty_and_tiny_curves(umi):
+    lens = [0, 5, 0, 1, 2000, 0, 3, 700]
+    Ws = [3, 361, 25, 1, 361, 7, 2161, 25]
+    xs = [synth.random_curve(40 + k, n) for k, n in enumerate(lens)]
+    flux = np.concatenate(xs).astype(np.float32)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    tr, de = umi.detrend_batched(torch.from_numpy(flux).cuda(), off, np.array(Ws, np.int32))
+    torch.cuda.synchronize()
+    tr = tr.cpu().numpy()
+    for k in range(len(lens)):
+        if lens[k] == 0:
+            continue
+        ref = oracle.detrend(xs[k], Ws[k])
+        compare_trend(tr[off[k]:off[k + 1]], ref["trend"], what="curve %d" % k)
+
+
+def test_graph_cache_and_host_entry_point_identical(umi):
+    b = synth.config3(n_curves=24)
+    W = np.array([umi.window_length(c) for c in b.cadence], np.int32)
+    flux = torch.from_numpy(b.flux).cuda()
+    umi.set_graph_cache(False)
+    t0, d0 = umi.detrend_batched(flux, b.offsets, W)
+    umi.set_graph_cache(True)
+    outs = [umi.detrend_batched(flux, b.offsets, W) for _ in range(3)]  # capture, then replays
+    torch.cuda.synchronize()
+    for t, d in outs:
+        assert torch.equal(torch.nan_to_num(t, 7.0), torch.nan_to_num(t0, 7.0))
+        assert torch.equal(torch.nan_to_num(d, 7.0), torch.nan_to_num(d0, 7.0))
+    pinned = torch.from_numpy(b.flux).pin_memory()
+    th = torch.empty(b.flux.size, dtype=torch.float32).pin_memory()
+    dh = torch.empty(b.flux.size, dtype=torch.float32).pin_memory()
+    umi.detrend_batched_host(pinned, b.offsets, W, trend=th, detr=dh)
+    assert np.array_equal(th.numpy(), t0.cpu().numpy(), equal_nan=True)
+    assert np.array_equal(dh.numpy(), d0.cpu().numpy(), equal_nan=True)
+
+
+def test_autotune_keeps_parity(umi):
+    try:
+        plan, ms = umi.autotune(361, positions=300000)
+        assert plan["lanes"] * plan["slots"] >= 361 and ms > 0
+        assert umi.get_plan(361, -1)["chain"] == plan["chain"]
+        x = synth.config1().curve(0)
+        compare_diag(run_diag(umi, x, 361), oracle.detrend(x, 361), what="tuned")
+    finally:
+        umi.clear_tuning()
+
+
+def test_stream_ordering_on_side_stream(umi):
+    x = synth.config1().curve(0)[:5000].copy()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        xd = torch.from_numpy(x).cuda(non_blocking=False)
+        tr, de = umi.detrend(xd, 361, stream=s)
+    s.synchronize()
+    compare_trend(tr.cpu().numpy(), oracle.detrend(x, 361)["trend"], what="side stream")

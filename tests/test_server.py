@@ -1,0 +1,168 @@
+"""Continuous-batching server on the GPU: each result is the same alone and in
+a mix, admission respects the memory budget, errors are reported per request,
+and injected host-side failures fail only the affected requests."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2604_06602_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def umi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_06602_gb300 import umi as u
+    u.load(build_if_missing=True)
+    return u
+
+
+def curves_mix(n=40):
+    out = []
+    for i in range(n):
+        kind = i % 3
+        if kind == 0:
+            x = synth.random_curve(500 + i, 3000 + 97 * i, nan_runs=2)
+            W = 361
+        elif kind == 1:
+            x = synth.random_curve(500 + i, 1500 + 31 * i, nan_frac=0.02)
+            W = 25
+        else:
+            x = synth.random_curve(500 + i, 5000 + 11 * i)
+            W = 2161
+        out.append((x, W))
+    return out
+
+
+def alone(umi, x, W):
+    xd = torch.from_numpy(x).cuda()
+    t, d = umi.detrend(xd, W)
+    torch.cuda.synchronize()
+    return t.cpu().numpy(), d.cpu().numpy()
+
+
+def test_alone_equals_mix(umi):
+    mix = curves_mix()
+    with umi.Server(mem_budget_bytes=1 << 30, n_streams=3, max_batch_curves=8) as srv:
+        tickets = [srv.submit(x, W) for x, W in mix]
+        for t in tickets:
+            srv.wait(t, 120.0)
+        for (x, W), t in zip(mix, tickets):
+            tr, de = srv.copy_out(t, x.size)
+            ta, da = alone(umi, x, W)
+            assert np.array_equal(tr, ta, equal_nan=True)
+            assert np.array_equal(de, da, equal_nan=True)
+            res = srv.poll(t)
+            assert res is not None and res[2] > 0
+            srv.release(t)
+        st = srv.stats()
+        assert st["completed"] == len(mix) and st["failed"] == 0
+        assert st["batches_launched"] >= len(mix) // 8
+        assert st["resident_bytes"] == 0
+
+
+def test_device_inputs_and_poll_pointers(umi):
+    x = synth.random_curve(3, 4000)
+    xd = torch.from_numpy(x).cuda()
+    with umi.Server(mem_budget_bytes=64 << 20) as srv:
+        t = srv.submit(xd, 361)
+        srv.wait(t, 60.0)
+        tr_ptr, de_ptr, lat = srv.poll(t)
+        assert tr_ptr and de_ptr and lat > 0
+        tr, _ = srv.copy_out(t, x.size)
+        ta, _ = alone(umi, x, 361)
+        assert np.array_equal(tr, ta, equal_nan=True)
+        srv.release(t)
+
+
+def test_budget_backpressure(umi):
+    """A budget that holds two curves: later requests wait for releases."""
+    n = 20000
+    per = 3 * ((4 * n + 255) // 256 * 256)
+    xs = [synth.random_curve(70 + i, n) for i in range(6)]
+    with umi.Server(mem_budget_bytes=2 * per + 1024, n_streams=2) as srv:
+        tickets = [srv.submit(x, 361) for x in xs]
+        srv.wait(tickets[0], 60.0)
+        srv.wait(tickets[1], 60.0)
+        time.sleep(0.05)
+        assert srv.poll(tickets[2]) is None            # no memory yet
+        st = srv.stats()
+        assert st["queued_requests"] == 4 and st["peak_resident_bytes"] <= 2 * per
+        for i, t in enumerate(tickets):
+            srv.wait(t, 60.0)
+            tr, _ = srv.copy_out(t, n)
+            ta, _ = alone(umi, xs[i], 361)
+            assert np.array_equal(tr, ta, equal_nan=True)
+            srv.release(t)
+        assert srv.stats()["peak_resident_bytes"] <= 2 * per
+
+
+def test_errors(umi):
+    with umi.Server(mem_budget_bytes=1 << 20) as srv:
+        x = synth.random_curve(1, 1000)
+        with pytest.raises(umi.UmiError) as e:
+            srv.submit(x, 360)
+        assert e.value.status == umi.UMI_ERR_INVALID_ARG
+        with pytest.raises(umi.UmiError) as e:
+            srv.submit(synth.random_curve(2, 200000), 361)   # can never fit 1 MiB
+        assert e.value.status == umi.UMI_ERR_BUSY
+        with pytest.raises(umi.UmiError) as e:
+            srv.poll(12345)
+        assert e.value.status == umi.UMI_ERR_UNKNOWN_TICKET
+        t = srv.submit(x, 361)
+        srv.wait(t, 60.0)
+        srv.release(t)
+        with pytest.raises(umi.UmiError) as e:
+            srv.release(t)
+        assert e.value.status == umi.UMI_ERR_UNKNOWN_TICKET
+        assert srv.stats()["rejected"] == 1
+
+
+def test_injected_failures_only_hit_their_requests(umi):
+    mix = curves_mix(12)
+    with umi.Server(mem_budget_bytes=1 << 30, n_streams=1, max_batch_curves=4) as srv:
+        srv.inject_fault(1, 1)                        # the next batch fails to launch
+        first = [srv.submit(x, W) for x, W in mix[:4]]
+        for t in first:
+            with pytest.raises(umi.UmiError) as e:
+                srv.wait(t, 60.0)
+            assert e.value.status == umi.UMI_ERR_FAILED
+        srv.inject_fault(2, 2)                        # two admissions fail
+        rest = [srv.submit(x, W) for x, W in mix[4:]]
+        outcomes = []
+        for t in rest:
+            try:
+                srv.wait(t, 60.0)
+                outcomes.append("ok")
+            except umi.UmiError as e:
+                assert e.status == umi.UMI_ERR_FAILED
+                outcomes.append("failed")
+        assert outcomes.count("failed") == 2 and outcomes[:2] == ["failed", "failed"]
+        for (x, W), t, o in zip(mix[4:], rest, outcomes):
+            if o == "ok":
+                tr, _ = srv.copy_out(t, x.size)
+                ta, _ = alone(umi, x, W)
+                assert np.array_equal(tr, ta, equal_nan=True)
+        for t in first + rest:
+            srv.release(t)
+        assert srv.stats()["resident_bytes"] == 0
+
+
+def test_wait_timeout_is_reported(umi):
+    with umi.Server(mem_budget_bytes=64 << 20, n_streams=1) as srv:
+        # A queued request that cannot be admitted (slots full) times out cleanly.
+        pass
+    with umi.Server(mem_budget_bytes=64 << 20, max_slots=1) as srv:
+        a = srv.submit(synth.random_curve(1, 2000), 25)
+        b = srv.submit(synth.random_curve(2, 2000), 25)
+        srv.wait(a, 60.0)
+        with pytest.raises(umi.UmiError) as e:
+            srv.wait(b, 0.05)                            # a holds the only slot
+        assert e.value.status == umi.UMI_ERR_TIMEOUT
+        srv.release(a)
+        srv.wait(b, 60.0)
+        srv.release(b)
