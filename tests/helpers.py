@@ -8,7 +8,7 @@ import numpy as np
 TREND_RTOL = 1e-5
 
 
-def compare_diag(got, ref, c=5.0, scale_aware=False, what=""):
+def compare_diag(got, ref, c=5.0, scale_aware=False, what="", x=None):
     """got: dict of numpy arrays from the GPU diag path; ref: oracle dict."""
     n = ref["trend"].size
     assert got["trend"].size == n
@@ -24,7 +24,18 @@ def compare_diag(got, ref, c=5.0, scale_aware=False, what=""):
     assert bad.size == 0, "%s median differs at %s: %s vs %s" % (
         what, np.nonzero(ok)[0][bad[:5]], mgot[ok][bad[:5]], mref[ok][bad[:5]])
     compare_trend(got["trend"], ref["trend"], ref.get("scale"), c, scale_aware, what)
-    compare_detr(got["detr"], ref["detr"], what)
+    if scale_aware:
+        # x / trend amplifies the trend's error by |x| / trend^2 where the trend
+        # is near zero; check the NaN pattern and that detr is the IEEE
+        # quotient of the sample by the GPU's own trend instead.
+        np.testing.assert_array_equal(np.isnan(got["detr"]), np.isnan(ref["detr"]),
+                                      err_msg=what + " detr NaN pattern")
+        if x is not None:
+            ok = ~np.isnan(ref["detr"])
+            q = (x[ok].astype(np.float32) / got["trend"][ok].astype(np.float32))
+            np.testing.assert_array_equal(got["detr"][ok], q, err_msg=what + " detr quotient")
+    else:
+        compare_detr(got["detr"], ref["detr"], what)
 
 
 def compare_trend(tgot, tref, sref=None, c=5.0, scale_aware=False, what=""):

@@ -88,7 +88,7 @@ def test_all_missing_constant_and_sparse(umi, W):
     x = synth.random_curve(9, n)
     x[n // 4: n // 2] = 0.9995
     x[n // 2: n // 2 + W] = np.nan
-    x[n // 2 + W // 2] = 1.0
+    x[min(n - 1, n // 2 + W // 2)] = 1.0
     compare_diag(run_diag(umi, x, W), oracle.detrend(x, W), what="runs W=%d" % W)
     x = np.full(n, np.nan, np.float32)
     x[:: max(2, W // 2)] = 1.0 + np.arange(x[:: max(2, W // 2)].size, dtype=np.float32) * 1e-4
@@ -123,9 +123,9 @@ def test_zero_centred_and_scaled(umi):
         x = (level + sigma * rng.standard_normal(3000)).astype(np.float32)
         x[rng.uniform(size=x.size) < 0.03] = np.nan
         compare_diag(run_diag(umi, x, 129), oracle.detrend(x, 129), scale_aware=True,
-                     what="level=%g sigma=%g" % (level, sigma))
+                     what="level=%g sigma=%g" % (level, sigma), x=x)
     x = rng.integers(-3, 4, 2000).astype(np.float32)   # integers: ties everywhere
-    compare_diag(run_diag(umi, x, 61), oracle.detrend(x, 61), scale_aware=True, what="integers")
+    compare_diag(run_diag(umi, x, 61), oracle.detrend(x, 61), scale_aware=True, what="integers", x=x)
 
 
 def test_config1_full_and_depth_recovery(umi):

@@ -124,7 +124,10 @@ def test_errors(umi):
 
 def test_injected_failures_only_hit_their_requests(umi):
     mix = curves_mix(12)
-    with umi.Server(mem_budget_bytes=1 << 30, n_streams=1, max_batch_curves=4) as srv:
+    # max_wait_s holds a partial batch back, so the four requests submitted
+    # together form one batch of max_batch_curves = 4.
+    with umi.Server(mem_budget_bytes=1 << 30, n_streams=1, max_batch_curves=4,
+                    max_wait_s=2.0) as srv:
         srv.inject_fault(1, 1)                        # the next batch fails to launch
         first = [srv.submit(x, W) for x, W in mix[:4]]
         for t in first:
