@@ -126,6 +126,42 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
                                     const int32_t *W_h, int32_t B, const umi_params *params,
                                     float *trend_h, float *detr_h, void *stream);
 
+/* Capacity of the fixed device array behind umi_detrend_batched_noalloc. */
+#define UMI_NOALLOC_SCRATCH_BYTES (4u * 1024u * 1024u)
+
+/*
+ * umi_detrend_batched for callers that cannot allocate device memory.  The
+ * paper has no counterpart to this entry point; it exists for the library's
+ * users.  Some callers cannot call cudaMalloc or cudaMallocAsync at the point
+ * where they detrend: a host application whose device memory is already
+ * reserved in full by another framework's caching allocator, a real-time
+ * pipeline that forbids allocation after start-up (cudaMalloc and cudaFree
+ * may synchronise the device and block for an unbounded time), or a
+ * deployment where the stream-ordered memory pool is disabled.  This call
+ * runs the same batched work-queue kernel, but its work-queue tables (curve
+ * descriptors, tile items, counters) live in one file-scope device array of
+ * UMI_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU loading libumi holds until
+ * the process exits.  The caller still passes the input and output buffers.
+ *   - It calls no cudaMalloc, cudaMallocAsync, cudaFree or other device
+ *     allocator, and does not use the CUDA-graph cache.
+ *   - A batch whose tables need more than UMI_NOALLOC_SCRATCH_BYTES returns
+ *     UMI_ERR_INVALID_ARG with the size in umi_last_error(); about 48 bytes
+ *     per curve plus 8 bytes per tile (roughly 90k curves of 18,000 samples
+ *     at W = 361); split larger batches.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array, which keeps the last call's tables;
+ *     each call rewrites the tables and clears its counters on `stream`
+ *     before its kernels run.  Calls whose work overlaps on the GPU (for
+ *     example on two streams at once) race on the array: order them on one
+ *     stream or serialise them.
+ * Arguments, validation and results are those of umi_detrend_batched.
+ */
+umi_status umi_detrend_batched_noalloc(const float *flux_d, const int64_t *offsets_h,
+                                       const int32_t *W_h, int32_t B, const umi_params *params,
+                                       float *trend_d, float *detr_d, void *stream);
+
 /*
  * Diagnostic form of umi_detrend, for parity checks.  Besides trend and
  * detr it writes, per position:

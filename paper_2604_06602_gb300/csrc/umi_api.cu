@@ -611,6 +611,91 @@ static umi_status time_plan(const Plan &plan, const float *flux, float *trend, f
     return st;
 }
 
+// ------------------------------------------------ allocation-free batch --
+// The work-queue tables of umi_detrend_batched_noalloc live in this fixed
+// array instead of stream-ordered allocations.  Host code must not pass the
+// array's name to a kernel (on the host it names a shadow variable); it looks
+// up the device address once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[UMI_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static std::map<int, void *> g_noalloc_addr;  // device ordinal -> address of the array
+
+static umi_status noalloc_scratch_address(void **out)
+{
+    const int dev = current_device();
+    if (dev < 0) return fail(UMI_ERR_CUDA, "no current CUDA device");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(dev);
+    if (it != g_noalloc_addr.end()) {
+        *out = it->second;
+        return UMI_OK;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetSymbolAddress (no-alloc scratch)");
+    g_noalloc_addr[dev] = p;
+    *out = p;
+    return UMI_OK;
+}
+
+static umi_status noalloc_batched(const float *flux, const int64_t *offsets, const int32_t *W,
+                                  int32_t B, const umi_params *params, float *trend, float *detr,
+                                  cudaStream_t stream)
+{
+    clear_error();
+    umi_params p;
+    umi_status st = check_params(params, &p);
+    if (st != UMI_OK) return st;
+    if (B < 0) return fail(UMI_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return UMI_OK;
+    if (!offsets || !W) return fail(UMI_ERR_INVALID_ARG, "null offsets or W");
+    if (offsets[0] != 0) return fail(UMI_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int32_t b = 0; b < B; ++b) {
+        if (offsets[b + 1] < offsets[b]) return fail(UMI_ERR_INVALID_ARG, "offsets must be non-decreasing");
+        if (W[b] < 1 || (W[b] % 2) == 0 || W[b] > kMaxWindow)
+            return fail(UMI_ERR_INVALID_ARG, "W[" + std::to_string(b) + "] must be odd and in [1, " +
+                                                 std::to_string(kMaxWindow) + "]");
+    }
+    if (offsets[B] == 0) return UMI_OK;
+    if (!flux || !trend || !detr) return fail(UMI_ERR_INVALID_ARG, "null buffer");
+    std::vector<Curve> curves;
+    curves.reserve(B);
+    for (int32_t b = 0; b < B; ++b) {
+        const int64_t o = offsets[b], n = offsets[b + 1] - offsets[b];
+        if (n == 0) continue;
+        curves.push_back(make_curve(flux + o, trend + o, detr + o, n, W[b], p));
+    }
+    BatchLayout lay;
+    st = build_layout(curves, &lay);
+    if (st != UMI_OK) return st;
+    if (lay.items.empty()) return UMI_OK;
+    const Scratch sc = scratch_layout(curves.size(), lay.items.size(), lay.bands.size());
+    if (sc.bytes > UMI_NOALLOC_SCRATCH_BYTES)
+        return fail(UMI_ERR_INVALID_ARG,
+                    "batch needs " + std::to_string(sc.bytes) + " bytes of work-queue tables, above the " +
+                        std::to_string((size_t)UMI_NOALLOC_SCRATCH_BYTES) +
+                        "-byte no-alloc scratch; split the batch");
+    for (const auto &band : lay.bands) {
+        st = prepare_kernel(band.plan, false);
+        if (st != UMI_OK) return st;
+    }
+    void *dev = nullptr;
+    st = noalloc_scratch_address(&dev);
+    if (st != UMI_OK) return st;
+    std::vector<char> host(sc.counter_off);
+    memcpy(host.data() + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
+    memcpy(host.data() + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
+    // Stream-ordered after any earlier call's kernels on this stream; the
+    // pageable source may be freed once the call returns.
+    UMI_CUDA(cudaMemcpyAsync(dev, host.data(), sc.counter_off, cudaMemcpyHostToDevice, stream),
+             "cudaMemcpyAsync (no-alloc tables)");
+    int launches = 0;
+    st = enqueue_bands(lay, (char *)dev, sc, stream, &launches);  // clears the counters first
+    g_kernel_launches += launches;
+    return st;
+}
+
 }  // namespace umi
 
 using namespace umi;
@@ -669,6 +754,13 @@ umi_status umi_detrend_batched(const float *flux_d, const int64_t *offsets_h, co
 {
     return batched_impl(flux_d, offsets_h, W_h, B, params, trend_d, detr_d, (cudaStream_t)stream,
                         true);
+}
+
+umi_status umi_detrend_batched_noalloc(const float *flux_d, const int64_t *offsets_h,
+                                       const int32_t *W_h, int32_t B, const umi_params *params,
+                                       float *trend_d, float *detr_d, void *stream)
+{
+    return noalloc_batched(flux_d, offsets_h, W_h, B, params, trend_d, detr_d, (cudaStream_t)stream);
 }
 
 umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_h,

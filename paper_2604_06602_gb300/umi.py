@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "UMI_OK", 1: "UMI_ERR_INVALID_ARG", 2: "UMI_ERR_CUDA", 3: "UM
 # Every function include/umi.h declares (checked by the ABI test).
 EXPORTS = [
     "umi_default_params", "umi_window_length", "umi_detrend", "umi_detrend_batched",
-    "umi_detrend_batched_host", "umi_detrend_diag", "umi_max_window", "umi_get_plan",
+    "umi_detrend_batched_host", "umi_detrend_batched_noalloc", "umi_detrend_diag", "umi_max_window", "umi_get_plan",
     "umi_autotune", "umi_save_tuning", "umi_load_tuning", "umi_clear_tuning",
     "umi_set_graph_cache", "umi_server_default_config", "umi_server_create", "umi_server_submit",
     "umi_server_poll", "umi_server_wait", "umi_server_copy_out", "umi_server_release",
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = False):
             "umi_detrend": (ctypes.c_int, [_vp, _i64, _i32, P(Params), _vp, _vp, _vp]),
             "umi_detrend_batched": (ctypes.c_int, [_vp, _vp, _vp, _i32, P(Params), _vp, _vp, _vp]),
             "umi_detrend_batched_host": (ctypes.c_int, [_vp, _vp, _vp, _i32, P(Params), _vp, _vp, _vp]),
+            "umi_detrend_batched_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i32, P(Params), _vp, _vp,
+                                                           _vp]),
             "umi_detrend_diag": (ctypes.c_int, [_vp, _i64, _i32, P(Params), _vp, _vp, _vp, _vp, _vp,
                                                 _vp, _vp]),
             "umi_max_window": (_i32, []),
@@ -249,6 +251,27 @@ def detrend_batched(flux, offsets, W, p: Params | None = None, trend=None, detr=
                                       None if p is None else ctypes.byref(p),
                                       _dev_f32(trend, "trend"), _dev_f32(detr, "detr"),
                                       _stream_handle(stream)))
+    return trend, detr
+
+
+def detrend_batched_noalloc(flux, offsets, W, p: Params | None = None, trend=None, detr=None,
+                            stream=None):
+    """CSR batch through umi_detrend_batched_noalloc: the library allocates no
+    device memory for it (its work-queue tables go to a fixed 4 MiB device
+    array), for callers that cannot allocate at this point.  Calls that
+    overlap on the GPU share that array; keep them on one stream."""
+    import torch
+    off, offp = _host_i64(offsets)
+    w, wp = _host_i32(W)
+    B = off.size - 1
+    if w.size != B:
+        raise ValueError("W must have one entry per curve")
+    trend = torch.empty_like(flux) if trend is None else trend
+    detr = torch.empty_like(flux) if detr is None else detr
+    _check(load().umi_detrend_batched_noalloc(_dev_f32(flux, "flux"), offp, wp, B,
+                                              None if p is None else ctypes.byref(p),
+                                              _dev_f32(trend, "trend"), _dev_f32(detr, "detr"),
+                                              _stream_handle(stream)))
     return trend, detr
 
 
