@@ -200,7 +200,8 @@ umi_status umi_get_plan(int32_t W, int64_t positions, umi_plan *plan);
  * window length W on a synthetic flux-like curve of `positions` samples on
  * `stream` (blocking), and records the fastest for W's band.  Later calls
  * use the recorded plan.  umi_save_tuning / umi_load_tuning persist the
- * table as text keyed by GPU name.
+ * table as text lines "gpu|W|G|R|MINB|chain|threads" keyed by GPU name
+ * (MINB: the register budget of the variant, in CTAs of 256 threads per SM).
  */
 umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *best,
                         double *best_ms);

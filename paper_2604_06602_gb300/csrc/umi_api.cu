@@ -102,15 +102,18 @@ static int default_chain(int G)
     case 1: return 33;
     case 2: return 34;
     case 4: return 36;
-    case 8: return 40;
-    case 16: return 48;
+    case 8: return 72;
+    case 16: return 80;
     default: return 64;
     }
 }
 
 // Tuned plans, keyed by window length (filled by umi_autotune / umi_load_tuning).
+// Every change bumps g_tune_epoch, which is part of the CUDA-graph cache key,
+// so a cached graph never replays a plan that is no longer current.
 static std::mutex g_tune_mu;
 static std::map<int, Plan> g_tuned;
+static std::atomic<uint64_t> g_tune_epoch{0};
 
 static int pick_variant(int W)
 {
@@ -265,7 +268,9 @@ static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const 
     int nv = 0;
     const Variant *t = variant_table(&nv);
     LaunchFn fn = use_diag ? t[plan.variant].launch_diag : t[plan.variant].launch;
-    cudaError_t e = fn(a, (int)items, plan.threads, plan.smem_bytes(), stream);
+    const int warps = plan.threads / 32;
+    const int64_t grid = (items + warps - 1) / warps;
+    cudaError_t e = fn(a, (int)grid, plan.threads, plan.smem_bytes(), stream);
     if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
     return UMI_OK;
 }
@@ -345,7 +350,8 @@ static umi_status enqueue_bands(const BatchLayout &lay, char *dev, const Scratch
         a.n_items = band.n_items;
         a.chain = band.plan.chain;
         a.queue = reinterpret_cast<int32_t *>(dev + sc.counter_off) + k;
-        const int grid = std::min(band.n_items, persistent_grid(band.plan, false));
+        const int warps = band.plan.threads / 32;
+        const int grid = std::min((band.n_items + warps - 1) / warps, persistent_grid(band.plan, false));
         cudaError_t e = t[band.plan.variant].launch(a, grid, band.plan.threads,
                                                     band.plan.smem_bytes(), stream);
         if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
@@ -400,6 +406,7 @@ struct GraphEntry {
     float *trend = nullptr, *detr = nullptr;
     umi_params params{};
     int device = -1;
+    uint64_t tune_epoch = 0;
     void *dev = nullptr;
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
@@ -502,7 +509,9 @@ static umi_status batched_impl(const float *flux, const int64_t *offsets, const 
         return st;
     }
     const int dev = current_device();
+    const uint64_t epoch = g_tune_epoch.load();
     uint64_t key = 1469598103934665603ull;
+    key = fnv1a(&epoch, sizeof(epoch), key);
     key = fnv1a(offsets, sizeof(int64_t) * (B + 1), key);
     key = fnv1a(W, sizeof(int32_t) * B, key);
     key = fnv1a(&p, sizeof(p), key);
@@ -513,7 +522,8 @@ static umi_status batched_impl(const float *flux, const int64_t *offsets, const 
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
         GraphEntry &g = *it;
-        if (g.key != key || g.device != dev || g.flux != flux || g.trend != trend || g.detr != detr ||
+        if (g.key != key || g.device != dev || g.tune_epoch != epoch || g.flux != flux ||
+            g.trend != trend || g.detr != detr ||
             (int32_t)g.W.size() != B || memcmp(&g.params, &p, sizeof(p)) != 0 ||
             memcmp(g.offsets.data(), offsets, sizeof(int64_t) * (B + 1)) != 0 ||
             memcmp(g.W.data(), W, sizeof(int32_t) * B) != 0)
@@ -532,6 +542,7 @@ static umi_status batched_impl(const float *flux, const int64_t *offsets, const 
     g.detr = detr;
     g.params = p;
     g.device = dev;
+    g.tune_epoch = epoch;
     st = build_graph(curves, &g);
     if (st != UMI_OK) {
         destroy_entry(g);
@@ -828,23 +839,27 @@ umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *be
     Plan best;
     double bms = 1e30;
     umi_status st = UMI_OK;
-    int eligible = 0;
+    // Candidates: every variant whose slot capacity fits W without wasting more
+    // than a third of it (the smallest fitting capacity always qualifies),
+    // two CTA sizes, and chain lengths of about 8 to 136 positions per group.
+    int smallest = 1 << 30;
+    for (int v = 0; v < nv; ++v)
+        if (t[v].G * t[v].R >= W) smallest = std::min(smallest, t[v].G * t[v].R);
     for (int v = 0; v < nv && st == UMI_OK; ++v) {
         const int S = t[v].G * t[v].R;
-        if (S < W) continue;
-        if (eligible >= 3) break;  // the three smallest capacities that fit
-        ++eligible;
+        if (S < W || (S > smallest && 3 * S > 4 * W)) continue;
         const int G = t[v].G;
         for (int threads : {128, 256}) {
-            if (threads < G) continue;
-            for (int mult : {1, 3, 5, 9}) {
+            int last_chain = -1;
+            for (int target : {8, 24, 40, 72, 136}) {
                 Plan p;
                 p.variant = v;
                 p.G = G;
                 p.R = t[v].R;
                 p.threads = threads;
-                p.chain = (G >= 32) ? 16 * mult : round_chain(G, G * mult * (G >= 8 ? 1 : 4));
-                if (!legal_chain(G, p.chain)) continue;
+                p.chain = round_chain(G, std::max(G, target));
+                if (p.chain == last_chain || !legal_chain(G, p.chain)) continue;
+                last_chain = p.chain;
                 if (p.smem_bytes() > device_info(current_device()).smem_optin) continue;
                 double ms = 0;
                 st = time_plan(p, buf, buf + positions, buf + 2 * positions, positions, W, s, &ms);
@@ -862,6 +877,7 @@ umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *be
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[W] = best;
+        ++g_tune_epoch;
     }
     if (best_out) {
         best_out->lanes = best.G;
@@ -882,10 +898,12 @@ umi_status umi_save_tuning(const char *path)
     if (!f) return fail(UMI_ERR_INVALID_ARG, std::string("cannot write ") + path);
     const std::string gpu = device_info(current_device()).name;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    f << "# umi tuning table: gpu|W|G|R|chain|threads\n";
+    int nv = 0;
+    const Variant *t = variant_table(&nv);
+    f << "# umi tuning table: gpu|W|G|R|MINB|chain|threads\n";
     for (auto &kv : g_tuned)
         f << gpu << "|" << kv.first << "|" << kv.second.G << "|" << kv.second.R << "|"
-          << kv.second.chain << "|" << kv.second.threads << "\n";
+          << t[kv.second.variant].minb << "|" << kv.second.chain << "|" << kv.second.threads << "\n";
     return UMI_OK;
 }
 
@@ -906,15 +924,16 @@ umi_status umi_load_tuning(const char *path)
         std::stringstream ss(line);
         std::string tok;
         while (std::getline(ss, tok, '|')) parts.push_back(tok);
-        if (parts.size() != 6 || parts[0] != gpu) continue;
+        if (parts.size() != 7 || parts[0] != gpu) continue;
         Plan p;
         const int W = std::atoi(parts[1].c_str());
         p.G = std::atoi(parts[2].c_str());
         p.R = std::atoi(parts[3].c_str());
-        p.chain = std::atoi(parts[4].c_str());
-        p.threads = std::atoi(parts[5].c_str());
+        const int minb = std::atoi(parts[4].c_str());
+        p.chain = std::atoi(parts[5].c_str());
+        p.threads = std::atoi(parts[6].c_str());
         for (int v = 0; v < nv; ++v)
-            if (t[v].G == p.G && t[v].R == p.R) p.variant = v;
+            if (t[v].G == p.G && t[v].R == p.R && t[v].minb == minb) p.variant = v;
         if (p.variant < 0 || W < 1 || (W % 2) == 0 || W > kMaxWindow || p.G * p.R < W ||
             !legal_chain(p.G, p.chain) || p.threads < p.G || p.threads > 256 || p.threads % 32)
             return fail(UMI_ERR_INVALID_ARG, "bad tuning line: " + line);
@@ -922,6 +941,7 @@ umi_status umi_load_tuning(const char *path)
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto &kv : loaded) g_tuned[kv.first] = kv.second;
+    ++g_tune_epoch;
     return UMI_OK;
 }
 
@@ -929,6 +949,7 @@ void umi_clear_tuning(void)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned.clear();
+    ++g_tune_epoch;
 }
 
 void umi_set_graph_cache(int enabled)

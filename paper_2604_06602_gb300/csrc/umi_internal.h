@@ -33,8 +33,12 @@ struct Plan {
     int G = 0, R = 0;
     int chain = 0;    // positions per group
     int threads = 0;  // per CTA
-    int tile() const { return (threads / G) * chain; }
-    size_t smem_bytes() const { return sizeof(float) * (size_t)(tile() + G * R - 1); }
+    // Positions per work item (one warp's tile).
+    int tile() const { return (32 / G) * chain; }
+    size_t smem_bytes() const
+    {
+        return sizeof(float) * (size_t)(threads / 32) * (size_t)(tile() + G * R - 1);
+    }
 };
 
 bool legal_chain(int G, int chain);

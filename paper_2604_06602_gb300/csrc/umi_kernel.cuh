@@ -7,9 +7,9 @@
 // detrended flux = x / mu.
 //
 // GPU design (not the paper's one-thread-per-window kernel, Section 2.6):
-//  * A CTA owns a tile of T consecutive positions of one curve and stages the
-//    T + S - 1 samples its windows touch into shared memory once; missing
-//    samples (non-finite, or outside the curve) become kGap.
+//  * A warp owns a tile of T consecutive positions of one curve and stages the
+//    T + S - 1 samples its windows touch into its slice of shared memory once;
+//    missing samples (non-finite, or outside the curve) become kGap.
 //  * A "group" of G lanes (G = 1..32, a power of two) evaluates one window at a
 //    time, each lane holding R window slots in registers (S = G*R >= W slots;
 //    slots past W hold kGap).  The 32/G groups of a warp run in lock step on
@@ -24,12 +24,13 @@
 //    the last two take one pass over the registers.  Every median is the exact
 //    order statistic of rank floor((n_valid - 1)/2).
 //  * Eq. 1 is one pass over the registers, G+ comes from the counts.
-//  * Phase 3 keeps y = x - m in registers and runs the fixed number of steps
-//    on mu = m + delta: per slot r = y - delta, q = r*a + |r|*b (a, b fold the
-//    asymmetry of Eq. 2 and 1/(c s)), z = sat(1 - q^2), w = z^2 (Eq. 3), and
-//    the centred sums sum(w), sum(w r) give delta += sum(w r)/sum(w) (Eq. 4).
-//    A kGap slot has |q| >= 1 (or q overflows / is NaN), so sat() makes its
-//    weight exactly 0 without a mask.
+//  * Phase 3 keeps y = x - m in registers, in pairs for the packed FP32x2
+//    instructions, and runs the fixed number of steps on mu = m + delta: per
+//    slot u_eff = min(y kp - delta kp, y kn - delta kn) (kp = 1/(c s),
+//    kn = alpha/(c s): Eq. 2 without a branch), z = sat(1 - u_eff^2),
+//    w = z^2 (Eq. 3), and delta = sum(w y)/sum(w) (Eq. 4 about m).  A kGap
+//    slot has |u_eff| >= 1 (or it overflows), so sat() makes its weight
+//    exactly 0 without a mask.
 #pragma once
 
 #include <cstdint>
@@ -132,6 +133,14 @@ __device__ __forceinline__ unsigned group_umax(unsigned v)
     }
 }
 
+// d = clamp(a*b + c, 0, 1), NaN -> 0, as one saturating FMA.
+__device__ __forceinline__ float fma_sat(float a, float b, float c)
+{
+    float d;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // Order-preserving map from non-NaN floats to unsigned keys (-0 sorts just
 // below +0; the counts that follow compare floats, where they are equal).
 __device__ __forceinline__ unsigned float_key(float f)
@@ -147,27 +156,35 @@ __device__ __forceinline__ float key_float(unsigned k)
 }
 
 // Load the window of tile position q into registers: slot s = glane + G*i
-// holds tile[q + s] for s < W, kGap past W.  `tail_only` (uniform) says that
-// G*(R-1) < W, so only the last register row can hold slots past W; the
-// general path re-derives each row's limit from an opaque register so the
-// compiler does not keep R loop-invariant predicates alive across the chain.
+// holds tile[q + s] for s < W, kGap past W.  Slots are stored in pairs
+// (i = 2k, 2k+1 in x[k].x, x[k].y) for the packed FP32x2 arithmetic.
+// `tail_only` (uniform) says that G*(R-1) < W, so only the last register row
+// can hold slots past W; the general path re-derives each row's limit from an
+// opaque register so the compiler does not keep R loop-invariant predicates
+// alive across the chain.
 template <int G, int R>
-__device__ __forceinline__ void load_window(float (&x)[R], const float *tile, int q, int glane,
+__device__ __forceinline__ void load_window(float2 (&x)[R / 2], const float *tile, int q, int glane,
                                             int W, bool tail_only)
 {
     const float *base = tile + q + glane;
     if (tail_only) {
 #pragma unroll
-        for (int i = 0; i < R - 1; ++i) x[i] = base[G * i];
+        for (int k = 0; k < R / 2 - 1; ++k) {
+            x[k].x = base[G * (2 * k)];
+            x[k].y = base[G * (2 * k + 1)];
+        }
+        x[R / 2 - 1].x = base[G * (R - 2)];
         const float v = base[G * (R - 1)];
-        x[R - 1] = (glane + G * (R - 1) < W) ? v : kGap;
+        x[R / 2 - 1].y = (glane + G * (R - 1) < W) ? v : kGap;
     } else {
         int lim = W - glane;  // slot row i is valid for this lane iff G*i < lim
         asm volatile("" : "+r"(lim));
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const float v = base[G * i];
-            x[i] = (G * i < lim) ? v : kGap;
+        for (int k = 0; k < R / 2; ++k) {
+            const float a = base[G * (2 * k)];
+            const float b = base[G * (2 * k + 1)];
+            x[k].x = (G * (2 * k) < lim) ? a : kGap;
+            x[k].y = (G * (2 * k + 1) < lim) ? b : kGap;
         }
     }
 }
@@ -193,7 +210,8 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
     const float cst = cv.c;
     const int iters = cv.iters;
     const bool tail_only = G * (R - 1) < W;
-    float x[R];
+    static_assert(R % 2 == 0, "slots are processed in pairs");
+    float2 x[R / 2];
     MedianState st;
     st.m = 0.f;
     st.L = st.E = st.Gp = 0;
@@ -231,7 +249,8 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
         if (t == 0) {
             int c = 0;
 #pragma unroll
-            for (int i = 0; i < R; ++i) c += (x[i] > kGapLimit) ? 1 : 0;
+            for (int k = 0; k < R / 2; ++k)
+                c += ((x[k].x > kGapLimit) ? 1 : 0) + ((x[k].y > kGapLimit) ? 1 : 0);
             st.nv = group_sum_int<G>(c);
         }
         if (st.nv == 0) st.have = false;
@@ -284,9 +303,9 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             const float mf = key_float(res);
             int cl = 0, ce = 0;
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                cl += (x[i] < mf) ? 1 : 0;
-                ce += (x[i] == mf) ? 1 : 0;
+            for (int k = 0; k < R / 2; ++k) {
+                cl += ((x[k].x < mf) ? 1 : 0) + ((x[k].y < mf) ? 1 : 0);
+                ce += ((x[k].x == mf) ? 1 : 0) + ((x[k].y == mf) ? 1 : 0);
             }
             cl = group_sum_int<G>(cl);
             ce = group_sum_int<G>(ce);
@@ -302,18 +321,21 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
         // ---- one-rank move of the median -----------------------------------
         if (__any_sync(0xffffffffu, move != 0)) {
             const float sg = (move < 0) ? -1.f : 1.f;
+            const float2 sg2 = make_float2(sg, sg);
             const float sm = sg * st.m;
             float best = -INFINITY;
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const float y = sg * x[i];
-                best = (y < sm) ? fmaxf(best, y) : best;
+            for (int k = 0; k < R / 2; ++k) {
+                const float2 y = __fmul2_rn(x[k], sg2);
+                best = (y.x < sm) ? fmaxf(best, y.x) : best;
+                best = (y.y < sm) ? fmaxf(best, y.y) : best;
             }
             best = group_max<G>(best);
             const float cand = sg * best;
             int e = 0;
 #pragma unroll
-            for (int i = 0; i < R; ++i) e += (x[i] == cand) ? 1 : 0;
+            for (int k = 0; k < R / 2; ++k)
+                e += ((x[k].x == cand) ? 1 : 0) + ((x[k].y == cand) ? 1 : 0);
             e = group_sum_int<G>(e);
             if (move > 0) {
                 st.Gp += st.E;
@@ -336,36 +358,49 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
         float s = 0.f;
         if (__any_sync(0xffffffffu, produce)) {
             const float m = st.m;
-            float s2 = 0.f;
+            const float2 negm = make_float2(-m, -m);
+            float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                x[i] = x[i] - m;  // y = x - m, exact sign
-                const float yp = fmaxf(x[i], 0.f);
-                s2 = fmaf(yp, yp, s2);
+            for (int k = 0; k < R / 2; ++k) {
+                x[k] = __fadd2_rn(x[k], negm);  // y = x - m, exact sign
+                const float2 yp = make_float2(fmaxf(x[k].x, 0.f), fmaxf(x[k].y, 0.f));
+                s2 = __ffma2_rn(yp, yp, s2);
             }
-            s2 = group_sum<G>(s2);
-            s = (st.Gp > 0) ? kScaleFactor * sqrtf(s2 / (float)st.Gp) : 0.f;
+            const float s2sum = group_sum<G>(s2.x + s2.y);
+            s = (st.Gp > 0) ? kScaleFactor * sqrtf(s2sum / (float)st.Gp) : 0.f;
             const bool iterate = produce && (s > 0.f);
             if (__any_sync(0xffffffffu, iterate)) {
+                // u_eff of Eq. 2 is min(y kp - delta kp, y kn - delta kn) with
+                // kp = 1/(c s), kn = alpha/(c s) when alpha >= 1 (max when
+                // alpha < 1; negating both keeps one code path, and only u_eff^2
+                // is used).  Eq. 4 in centred form: delta_new = sum(w y)/sum(w)
+                // since mu = m + delta.
                 const float inv = 1.f / (cst * s);
-                const float ca = 0.5f * (1.f + alpha) * inv;  // q = r*ca + |r|*cb:
-                const float cb = 0.5f * (1.f - alpha) * inv;  // r/(cs) for r >= 0, alpha r/(cs) below
+                const float flip = (alpha >= 1.f) ? 1.f : -1.f;
+                const float kp = flip * inv;
+                const float kn = flip * alpha * inv;
+                const float2 kp2 = make_float2(kp, kp);
+                const float2 kn2 = make_float2(kn, kn);
                 float delta = 0.f;
 #pragma unroll 1
                 for (int it = 0; it < iters; ++it) {
-                    float sw = 0.f, swr = 0.f;
+                    const float2 c1 = make_float2(-delta * kp, -delta * kp);
+                    const float2 c2 = make_float2(-delta * kn, -delta * kn);
+                    float2 sw = make_float2(0.f, 0.f), swy = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int i = 0; i < R; ++i) {
-                        const float r = x[i] - delta;
-                        const float qv = fmaf(fabsf(r), cb, r * ca);
-                        const float z = __saturatef(fmaf(-qv, qv, 1.f));
-                        const float w = z * z;
-                        sw += w;
-                        swr = fmaf(w, r, swr);
+                    for (int k = 0; k < R / 2; ++k) {
+                        const float2 p1 = __ffma2_rn(x[k], kp2, c1);
+                        const float2 p2 = __ffma2_rn(x[k], kn2, c2);
+                        const float qa = fminf(p1.x, p2.x);
+                        const float qb = fminf(p1.y, p2.y);
+                        const float2 z = make_float2(fma_sat(-qa, qa, 1.f), fma_sat(-qb, qb, 1.f));
+                        const float2 w = __fmul2_rn(z, z);
+                        sw = __fadd2_rn(sw, w);
+                        swy = __ffma2_rn(w, x[k], swy);
                     }
-                    sw = group_sum<G>(sw);
-                    swr = group_sum<G>(swr);
-                    if (sw > 0.f) delta += swr / sw;
+                    const float sws = group_sum<G>(sw.x + sw.y);
+                    const float swys = group_sum<G>(swy.x + swy.y);
+                    if (sws > 0.f) delta = swys / sws;
                 }
                 if (iterate) mu = m + delta;
             }
@@ -385,31 +420,33 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
     }
 }
 
-// One CTA per work item (queue == nullptr) or a persistent CTA pulling items
-// from the queue counter.  Dynamic shared memory: (T + S - 1) floats,
-// T = (blockDim.x / G) * chain.
-template <int G, int R, bool DIAG>
-__global__ void __launch_bounds__(256) umi_tile_kernel(LaunchArgs a)
+// Work items belong to warps: each warp stages its own tile of T = (32/G)*P
+// positions (plus the S-1 halo samples) in its slice of shared memory, so no
+// CTA-wide barrier is ever needed.  Without a queue, warp w of CTA b takes
+// item b*warps + w; with a queue, each warp pulls items until none is left.
+// Dynamic shared memory: warps * (T + S - 1) floats.  MINB (CTAs of 256
+// threads per SM) sets the register budget the compiler aims for.
+template <int G, int R, int MINB, bool DIAG>
+__global__ void __launch_bounds__(256, MINB) umi_tile_kernel(LaunchArgs a)
 {
-    extern __shared__ float tile[];
-    __shared__ int s_item;
+    extern __shared__ float smem[];
     constexpr int S = G * R;
-    const int glane = threadIdx.x & (G - 1);
-    const int group = threadIdx.x / G;
-    const int n_groups = blockDim.x / G;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int n_warps = blockDim.x >> 5;
+    const int glane = lane & (G - 1);
+    const int group = lane / G;
     const int P = a.chain;
-    const int T = n_groups * P;
+    const int T = (32 / G) * P;
     const int tile_len = T + S - 1;
+    float *tile = smem + (size_t)warp * tile_len;
 
-    int next = blockIdx.x;
+    int item = blockIdx.x * n_warps + warp;
     for (;;) {
-        int item;
         if (a.queue) {
-            if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
-            __syncthreads();
-            item = s_item;
-        } else {
-            item = next;
+            int v = 0;
+            if (lane == 0) v = atomicAdd(a.queue, 1);
+            item = __shfl_sync(0xffffffffu, v, 0);
         }
         if (item >= a.n_items) break;
         const Item wi = a.items ? a.items[item] : Item{0, item};
@@ -417,7 +454,7 @@ __global__ void __launch_bounds__(256) umi_tile_kernel(LaunchArgs a)
         const int64_t t0 = (int64_t)wi.tile * T;
         const int h = (cv.W - 1) >> 1;
 
-        for (int k = threadIdx.x; k < tile_len; k += blockDim.x) {
+        for (int k = lane; k < tile_len; k += 32) {
             const int64_t idx = t0 - h + k;
             float v = kGap;
             if (idx >= 0 && idx < cv.n) {
@@ -426,9 +463,9 @@ __global__ void __launch_bounds__(256) umi_tile_kernel(LaunchArgs a)
             }
             tile[k] = v;
         }
-        __syncthreads();
+        __syncwarp();
         process_chain<G, R, DIAG>(cv, a.diag, tile, t0, group * P, P, glane);
-        __syncthreads();
+        __syncwarp();  // every lane is done with the tile before it is restaged
         if (!a.queue) break;
     }
 }

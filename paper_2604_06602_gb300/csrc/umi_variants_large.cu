@@ -1,5 +1,6 @@
-// Variants for long windows (W up to 4096): a full warp per window.
+// Variants for long windows (W up to 4096).
 #include "umi_variants.h"
-UMI_DEFINE_VARIANT(32, 48)
-UMI_DEFINE_VARIANT(32, 68)
-UMI_DEFINE_VARIANT(32, 128)
+UMI_DEFINE_VARIANT(16, 48, 2)
+UMI_DEFINE_VARIANT(32, 48, 2)
+UMI_DEFINE_VARIANT(32, 68, 2)
+UMI_DEFINE_VARIANT(32, 128, 1)

@@ -66,8 +66,8 @@ def compare_detr(dgot, dref, what=""):
 def depth_recovery_errors(detr, batch, idx=None):
     """Median-free per-curve depth recovery error (percent).
 
-    Reading of the paper's metric (median of per-star absolute percentage
-    errors, Section 3.2): recovered depth = median of detrended flux over the
+    Reading of the paper's metric (Section 3.2 aggregates each star's
+    absolute percentage depth error by a median over stars): recovered depth = median of detrended flux over the
     out-of-transit samples within one transit duration of each transit, minus
     the mean detrended flux inside transits; injected depth = mean injected
     profile over the same in-transit samples."""

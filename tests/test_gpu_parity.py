@@ -278,3 +278,29 @@ def test_stream_ordering_on_side_stream(umi):
         tr, de = umi.detrend(xd, 361, stream=s)
     s.synchronize()
     compare_trend(tr.cpu().numpy(), oracle.detrend(x, 361)["trend"], what="side stream")
+
+
+def test_graph_cache_follows_tuning_changes(umi, tmp_path):
+    """A cached graph must not replay a plan that tuning has since replaced."""
+    import torch as _t
+    b = synth.config2(n_curves=8, n=6000)
+    W = np.full(b.B, 361, np.int32)
+    flux = _t.from_numpy(b.flux).cuda()
+    tr = _t.empty_like(flux)
+    de = _t.empty_like(flux)
+    gpu = _t.cuda.get_device_name()
+    try:
+        umi.set_graph_cache(True)
+        umi.detrend_batched(flux, b.offsets, W, trend=tr, detr=de)
+        launches0 = umi.kernel_launch_count()
+        f = tmp_path / "tune.txt"
+        f.write_text("%s|361|32|12|4|24|128\n" % gpu)
+        umi.load_tuning(str(f))
+        assert umi.get_plan(361, -1)["lanes"] == 32
+        umi.detrend_batched(flux, b.offsets, W, trend=tr, detr=de)
+        _t.cuda.synchronize()
+        ref = oracle.detrend_batch(b.flux, b.offsets, W)[0]
+        compare_trend(tr.cpu().numpy(), ref, what="retuned graph")
+        assert umi.kernel_launch_count() > launches0
+    finally:
+        umi.clear_tuning()
