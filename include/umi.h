@@ -215,8 +215,9 @@ void umi_set_graph_cache(int enabled);
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of detrend requests under a device-memory
  * budget.  A scheduler thread admits queued requests while their resident
- * bytes (flux + trend + detr, 12 bytes per sample, plus alignment) fit the
- * budget and a slot is free, gathers the admitted requests into batched
+ * bytes (trend + detr, plus a copy of the flux for host inputs: 8 or 12 bytes
+ * per sample, plus alignment) fit the budget and a slot is free, gathers the
+ * admitted requests into batched
  * launches on `n_streams` streams so that batches overlap on the GPU, and
  * marks each request done when its batch's completion event fires.  Results
  * stay on the device until released.
@@ -239,6 +240,7 @@ typedef struct {
     uint64_t resident_bytes, peak_resident_bytes;
     uint64_t queued_requests;
     double mean_batch_curves;
+    double launch_host_s; /* scheduler time spent enqueuing batches (host seconds) */
 } umi_server_stats;
 
 void umi_server_default_config(umi_server_config *cfg);
@@ -248,11 +250,12 @@ umi_status umi_server_create(const umi_server_config *cfg, umi_server **out);
 
 /*
  * Queue one curve.  `flux` is a host pointer (is_device_ptr == 0) or a device
- * pointer (1); it is copied into server memory during admission, so the
- * caller may reuse its buffer once the ticket is done (host buffers: once
- * this call returns, because host data are copied into a staging buffer
- * first).  Returns UMI_ERR_BUSY if the request can never fit the budget,
- * UMI_ERR_INVALID_ARG for bad W/n/params.  `ticket` receives a non-zero id.
+ * pointer (1).  Host data are copied into a staging buffer before this call
+ * returns (the caller may reuse its buffer at once) and into server memory at
+ * launch.  Device data are read in place by the kernel: the caller keeps the
+ * buffer valid and unchanged until the ticket is done.  Returns UMI_ERR_BUSY
+ * if the request can never fit the budget, UMI_ERR_INVALID_ARG for bad
+ * W/n/params.  `ticket` receives a non-zero id.
  */
 umi_status umi_server_submit(umi_server *s, const float *flux, int is_device_ptr, int64_t n,
                              int32_t W, const umi_params *params, uint64_t *ticket);

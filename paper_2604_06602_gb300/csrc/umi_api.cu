@@ -361,6 +361,39 @@ static umi_status enqueue_bands(const BatchLayout &lay, char *dev, const Scratch
     return UMI_OK;
 }
 
+umi_status prepare_batch(const std::vector<Curve> &curves, PreparedBatch *pb)
+{
+    umi_status st = build_layout(curves, &pb->layout);
+    if (st != UMI_OK) return st;
+    for (const auto &band : pb->layout.bands) {
+        st = prepare_kernel(band.plan, false);
+        if (st != UMI_OK) return st;
+    }
+    const Scratch sc = scratch_layout(curves.size(), pb->layout.items.size(), pb->layout.bands.size());
+    pb->curve_off = sc.curve_off;
+    pb->item_off = sc.item_off;
+    pb->counter_off = sc.counter_off;
+    pb->dev_bytes = sc.bytes;
+    pb->host_bytes = sc.counter_off;
+    return UMI_OK;
+}
+
+umi_status enqueue_prepared(const std::vector<Curve> &curves, const PreparedBatch &pb, char *dev,
+                            char *host, cudaStream_t stream, int *launches)
+{
+    if (launches) *launches = 0;
+    if (pb.layout.items.empty()) return UMI_OK;
+    memcpy(host + pb.curve_off, curves.data(), curves.size() * sizeof(Curve));
+    memcpy(host + pb.item_off, pb.layout.items.data(), pb.layout.items.size() * sizeof(Item));
+    UMI_CUDA(cudaMemcpyAsync(dev, host, pb.host_bytes, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync");
+    Scratch sc;
+    sc.curve_off = pb.curve_off;
+    sc.item_off = pb.item_off;
+    sc.counter_off = pb.counter_off;
+    sc.bytes = pb.dev_bytes;
+    return enqueue_bands(pb.layout, dev, sc, stream, launches);
+}
+
 umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream, int *launches)
 {
     if (launches) *launches = 0;

@@ -69,4 +69,18 @@ struct BatchLayout {
 };
 umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout);
 
+// A batch planned for caller-owned buffers: `dev_bytes` of device scratch and
+// `host_bytes` of (preferably pinned) host staging for the tables.
+struct PreparedBatch {
+    BatchLayout layout;
+    size_t curve_off = 0, item_off = 0, counter_off = 0;
+    size_t dev_bytes = 0, host_bytes = 0;
+};
+umi_status prepare_batch(const std::vector<Curve> &curves, PreparedBatch *pb);
+// Stages the tables in `host`, copies them to `dev` on `stream`, clears the
+// counters and launches the bands.  The host buffer must stay untouched until
+// the copy has run (stream order).
+umi_status enqueue_prepared(const std::vector<Curve> &curves, const PreparedBatch &pb, char *dev,
+                            char *host, cudaStream_t stream, int *launches);
+
 }  // namespace umi

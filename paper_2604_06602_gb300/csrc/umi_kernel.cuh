@@ -386,7 +386,9 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                 for (int it = 0; it < iters; ++it) {
                     const float2 c1 = make_float2(-delta * kp, -delta * kp);
                     const float2 c2 = make_float2(-delta * kn, -delta * kn);
-                    float2 sw = make_float2(0.f, 0.f), swy = make_float2(0.f, 0.f);
+                    // Two accumulator pairs halve the dependent add chains.
+                    float2 sw[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    float2 swy[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
                     for (int k = 0; k < R / 2; ++k) {
                         const float2 p1 = __ffma2_rn(x[k], kp2, c1);
@@ -395,12 +397,16 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                         const float qb = fminf(p1.y, p2.y);
                         const float2 z = make_float2(fma_sat(-qa, qa, 1.f), fma_sat(-qb, qb, 1.f));
                         const float2 w = __fmul2_rn(z, z);
-                        sw = __fadd2_rn(sw, w);
-                        swy = __ffma2_rn(w, x[k], swy);
+                        sw[k & 1] = __fadd2_rn(sw[k & 1], w);
+                        swy[k & 1] = __ffma2_rn(w, x[k], swy[k & 1]);
                     }
-                    const float sws = group_sum<G>(sw.x + sw.y);
-                    const float swys = group_sum<G>(swy.x + swy.y);
-                    if (sws > 0.f) delta = swys / sws;
+                    const float2 swt = __fadd2_rn(sw[0], sw[1]);
+                    const float2 swyt = __fadd2_rn(swy[0], swy[1]);
+                    const float sws = group_sum<G>(swt.x + swt.y);
+                    const float swys = group_sum<G>(swyt.x + swyt.y);
+                    // sws <= S, so the fast quotient (2 ulp) is safe here; its
+                    // error is far below the FP32 rounding of the sums.
+                    if (sws > 0.f) delta = __fdividef(swys, sws);
                 }
                 if (iterate) mu = m + delta;
             }

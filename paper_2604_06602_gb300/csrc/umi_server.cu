@@ -3,11 +3,13 @@
 // Requests (one light curve each) are queued by umi_server_submit.  A
 // scheduler thread
 //   1. admits queued requests in arrival order while their resident memory
-//      (flux + trend + detr, each rounded up to 256 bytes) fits the arena and
+//      (trend + detr, plus flux for host inputs, each rounded up to 256 bytes)
+//      fits the arena and
 //      a slot is free; memory is handed out by a first-fit allocator over one
 //      cudaMalloc of the budget;
 //   2. gathers the admitted requests into one batch per idle stream (up to
-//      max_batch_curves), enqueues their input copies and one batched launch
+//      max_batch_curves), enqueues their host-input copies (device inputs are
+//      read in place) and one batched launch
 //      (the persistent work-queue kernel of umi_api.cu) on that stream, then a
 //      host callback that timestamps completion, so up to n_streams batches
 //      run on the GPU at once while new requests keep arriving;
@@ -95,6 +97,7 @@ struct Request {
     const float *dev_src = nullptr;  // input left on the device by the caller
     size_t off = 0, bytes = 0;       // arena range
     float *flux = nullptr, *trend = nullptr, *detr = nullptr;
+    bool admitted_mem = false;       // owns its arena range
     ReqState state = ReqState::Queued;
     double t_submit = 0, t_done = 0;
 };
@@ -111,11 +114,19 @@ struct Batch {
 
 using namespace umi;
 
+struct StreamBuffers {
+    char *dev = nullptr;   // work-queue tables of this stream's batch
+    size_t dev_bytes = 0;
+    char *host = nullptr;  // pinned staging for the tables
+    size_t host_bytes = 0;
+};
+
 struct umi_server {
     umi_server_config cfg{};
     char *arena = nullptr;
     std::unique_ptr<ArenaAllocator> alloc;
     std::vector<cudaStream_t> streams;
+    std::vector<StreamBuffers> bufs;  // one per stream; a stream runs one batch at a time
     std::vector<std::shared_ptr<Batch>> inflight;  // one slot per stream
     std::mutex mu;
     std::condition_variable cv_sched;
@@ -136,7 +147,11 @@ struct umi_server {
 namespace umi {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-static size_t request_bytes(int64_t n) { return 3 * align256(sizeof(float) * (size_t)n); }
+// Device-resident inputs are read in place, so they need no arena copy.
+static size_t request_bytes(int64_t n, bool device_input)
+{
+    return (device_input ? 2 : 3) * align256(sizeof(float) * (size_t)n);
+}
 
 static void CUDART_CB batch_done_cb(void *arg)
 {
@@ -177,9 +192,17 @@ static void admit_locked(umi_server *s)
         if (!s->alloc->alloc(r.bytes, &off)) break;  // head-of-line waits for memory
         r.off = off;
         const size_t one = align256(sizeof(float) * (size_t)r.n);
-        r.flux = reinterpret_cast<float *>(s->arena + off);
-        r.trend = reinterpret_cast<float *>(s->arena + off + one);
-        r.detr = reinterpret_cast<float *>(s->arena + off + 2 * one);
+        char *base = s->arena + off;
+        if (r.dev_src) {
+            r.flux = nullptr;
+            r.trend = reinterpret_cast<float *>(base);
+            r.detr = reinterpret_cast<float *>(base + one);
+        } else {
+            r.flux = reinterpret_cast<float *>(base);
+            r.trend = reinterpret_cast<float *>(base + one);
+            r.detr = reinterpret_cast<float *>(base + 2 * one);
+        }
+        r.admitted_mem = true;
         r.state = ReqState::Admitted;
         s->resident_slots++;
         s->stats.admitted++;
@@ -253,6 +276,7 @@ static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mute
     const bool inject = s->inject_launch_failures > 0;
     if (inject) --s->inject_launch_failures;
     lk.unlock();
+    const double t_enq0 = now_s();
 
     cudaStream_t st = s->streams[k];
     bool ok = !inject;
@@ -260,14 +284,13 @@ static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mute
     curves.reserve(jobs.size());
     for (auto &j : jobs) {
         if (!ok) break;
-        cudaError_t e;
-        if (j.src_dev)
-            e = cudaMemcpyAsync(j.flux, j.src_dev, sizeof(float) * j.n, cudaMemcpyDeviceToDevice, st);
-        else
-            e = cudaMemcpyAsync(j.flux, j.src_host.data(), sizeof(float) * j.n, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) ok = false;
+        if (!j.src_dev) {
+            const cudaError_t e = cudaMemcpyAsync(j.flux, j.src_host.data(), sizeof(float) * j.n,
+                                                  cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) ok = false;
+        }
         Curve c;
-        c.flux = j.flux;
+        c.flux = j.src_dev ? j.src_dev : j.flux;
         c.trend = j.trend;
         c.detr = j.detr;
         c.n = j.n;
@@ -280,10 +303,31 @@ static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mute
         curves.push_back(c);
     }
     int launches = 0;
-    if (ok && launch_curve_table(curves, st, &launches) != UMI_OK) ok = false;
+    PreparedBatch pb;
+    if (ok && prepare_batch(curves, &pb) != UMI_OK) ok = false;
+    StreamBuffers &sb = s->bufs[k];
+    // This stream's previous batch has completed (it is idle), so its buffers
+    // may be regrown or rewritten.
+    if (ok && pb.dev_bytes > sb.dev_bytes) {
+        if (sb.dev) cudaFree(sb.dev);
+        sb.dev = nullptr;
+        sb.dev_bytes = 0;
+        if (cudaMalloc((void **)&sb.dev, 2 * pb.dev_bytes) == cudaSuccess) sb.dev_bytes = 2 * pb.dev_bytes;
+        else ok = false;
+    }
+    if (ok && pb.host_bytes > sb.host_bytes) {
+        if (sb.host) cudaFreeHost(sb.host);
+        sb.host = nullptr;
+        sb.host_bytes = 0;
+        if (cudaMallocHost((void **)&sb.host, 2 * pb.host_bytes) == cudaSuccess) sb.host_bytes = 2 * pb.host_bytes;
+        else ok = false;
+    }
+    if (ok && enqueue_prepared(curves, pb, sb.dev, sb.host, st, &launches) != UMI_OK) ok = false;
     if (ok && cudaLaunchHostFunc(st, batch_done_cb, batch.get()) != cudaSuccess) ok = false;
+    const double t_enq = now_s() - t_enq0;
 
     lk.lock();
+    s->stats.launch_host_s += t_enq;
     s->stats.batches_launched++;
     s->batch_curves_sum += (double)take;
     s->stats.mean_batch_curves = s->batch_curves_sum / (double)s->stats.batches_launched;
@@ -361,6 +405,7 @@ umi_status umi_server_create(const umi_server_config *cfg_in, umi_server **out)
     if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc (server arena)");
     s->alloc.reset(new ArenaAllocator(cfg.mem_budget_bytes));
     s->streams.resize(cfg.n_streams);
+    s->bufs.resize(cfg.n_streams);
     s->inflight.resize(cfg.n_streams);
     for (auto &st : s->streams) {
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -391,7 +436,7 @@ umi_status umi_server_submit(umi_server *s, const float *flux, int is_device_ptr
     Plan plan;
     st = make_plan(W, -1, &plan);
     if (st != UMI_OK) return st;
-    const size_t bytes = request_bytes(n);
+    const size_t bytes = request_bytes(n, is_device_ptr != 0);
     if (bytes > s->cfg.mem_budget_bytes) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stats.rejected++;
@@ -498,7 +543,7 @@ umi_status umi_server_release(umi_server *s, uint64_t ticket)
             s->admitted.erase(std::remove(s->admitted.begin(), s->admitted.end(), ticket),
                               s->admitted.end());
         }
-        if (r.flux) {  // admitted at some point: owns arena memory
+        if (r.admitted_mem) {  // admitted at some point: owns arena memory
             s->alloc->release(r.off, r.bytes);
             s->resident_slots--;
             s->stats.resident_bytes = s->alloc->used();
@@ -545,6 +590,10 @@ void umi_server_destroy(umi_server *s)
     for (auto &st : s->streams) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
+    }
+    for (auto &b : s->bufs) {
+        if (b.dev) cudaFree(b.dev);
+        if (b.host) cudaFreeHost(b.host);
     }
     s->inflight.clear();
     if (s->arena) cudaFree(s->arena);

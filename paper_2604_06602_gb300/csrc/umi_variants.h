@@ -73,7 +73,6 @@ const Variant *variant_table(int *count);
     X(4, 32, 3)             \
     X(8, 24, 3)             \
     X(8, 46, 2)             \
-    X(8, 46, 3)             \
     X(16, 24, 4)            \
     X(32, 12, 4)            \
     X(16, 48, 2)            \

@@ -75,7 +75,7 @@ class ServerStats(ctypes.Structure):
                 ("rejected", ctypes.c_uint64), ("released", ctypes.c_uint64),
                 ("batches_launched", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64),
                 ("peak_resident_bytes", ctypes.c_uint64), ("queued_requests", ctypes.c_uint64),
-                ("mean_batch_curves", ctypes.c_double)]
+                ("mean_batch_curves", ctypes.c_double), ("launch_host_s", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
