@@ -102,7 +102,7 @@ static int default_chain(int G)
     case 1: return 33;
     case 2: return 34;
     case 4: return 36;
-    case 8: return 72;
+    case 8: return 136;
     case 16: return 80;
     default: return 64;
     }

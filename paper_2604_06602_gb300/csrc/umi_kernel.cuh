@@ -158,7 +158,7 @@ __device__ __forceinline__ float key_float(unsigned k)
 // Load the window of tile position q into registers: slot s = glane + G*i
 // holds tile[q + s] for s < W, kGap past W.  Slots are stored in pairs
 // (i = 2k, 2k+1 in x[k].x, x[k].y) for the packed FP32x2 arithmetic.
-// `tail_only` (uniform) says that G*(R-1) < W, so only the last register row
+// `tail_only` (uniform) says that G*(R-1) <= W, so only the last register row
 // can hold slots past W; the general path re-derives each row's limit from an
 // opaque register so the compiler does not keep R loop-invariant predicates
 // alive across the chain.
@@ -209,7 +209,7 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
     const float alpha = cv.alpha;
     const float cst = cv.c;
     const int iters = cv.iters;
-    const bool tail_only = G * (R - 1) < W;
+    const bool tail_only = G * (R - 1) <= W;  // rows 0..R-2 hold only slots < W
     static_assert(R % 2 == 0, "slots are processed in pairs");
     float2 x[R / 2];
     MedianState st;
@@ -386,9 +386,7 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                 for (int it = 0; it < iters; ++it) {
                     const float2 c1 = make_float2(-delta * kp, -delta * kp);
                     const float2 c2 = make_float2(-delta * kn, -delta * kn);
-                    // Two accumulator pairs halve the dependent add chains.
-                    float2 sw[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-                    float2 swy[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    float2 swt = make_float2(0.f, 0.f), swyt = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int k = 0; k < R / 2; ++k) {
                         const float2 p1 = __ffma2_rn(x[k], kp2, c1);
@@ -397,11 +395,9 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                         const float qb = fminf(p1.y, p2.y);
                         const float2 z = make_float2(fma_sat(-qa, qa, 1.f), fma_sat(-qb, qb, 1.f));
                         const float2 w = __fmul2_rn(z, z);
-                        sw[k & 1] = __fadd2_rn(sw[k & 1], w);
-                        swy[k & 1] = __ffma2_rn(w, x[k], swy[k & 1]);
+                        swt = __fadd2_rn(swt, w);
+                        swyt = __ffma2_rn(w, x[k], swyt);
                     }
-                    const float2 swt = __fadd2_rn(sw[0], sw[1]);
-                    const float2 swyt = __fadd2_rn(swy[0], swy[1]);
                     const float sws = group_sum<G>(swt.x + swt.y);
                     const float swys = group_sum<G>(swyt.x + swyt.y);
                     // sws <= S, so the fast quotient (2 ulp) is safe here; its

@@ -68,11 +68,13 @@ const Variant *variant_table(int *count);
 #define UMI_VARIANT_LIST(X) \
     X(1, 8, 4)              \
     X(1, 16, 4)             \
+    X(1, 26, 4)             \
     X(1, 32, 3)             \
     X(2, 32, 3)             \
     X(4, 32, 3)             \
     X(8, 24, 3)             \
     X(8, 46, 2)             \
+    X(8, 46, 3)             \
     X(16, 24, 4)            \
     X(32, 12, 4)            \
     X(16, 48, 2)            \

@@ -42,7 +42,10 @@ def tile_of(umi, W):
     return pl["threads"] // pl["lanes"] * pl["chain"]
 
 
-WINDOWS = [1, 3, 7, 25, 33, 129, 361, 369, 769, 1537, 2161, 4095]
+# Every variant's capacity edge (the last W a variant serves and the first W
+# of the next), plus the workload windows 25, 361 and 2161.
+WINDOWS = [1, 3, 7, 9, 15, 17, 25, 27, 31, 33, 63, 65, 127, 129, 191, 193, 361, 367, 369, 383,
+           385, 767, 769, 1535, 1537, 2161, 2175, 2177, 4095]
 
 
 @pytest.mark.parametrize("W", WINDOWS)
