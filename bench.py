@@ -52,7 +52,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="umi", choices=["umi", "reference"])
-    ap.add_argument("--curves", type=int, default=1000)
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"],
+                    help="c2 (default): 1000 TESS-like curves x 18000; c1: one such curve; "
+                         "c3: 4096 uneven TESS/Kepler curves; c4: 256 x 118000 at 20-s cadence")
+    ap.add_argument("--curves", type=int, default=None)
     ap.add_argument("--n", type=int, default=18000)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-curve, serving, e2e and CPU-baseline legs")
@@ -94,10 +97,28 @@ def barrier(dist):
         dist.barrier()
 
 
-def shard_seed(rank):
+def shard_seed(rank, config=1):
     """Each rank detrends its own batch: seeds differ per rank."""
     from paper_2604_06602_gb300 import synth
-    return synth.BASE_SEED + 1 + 1000 * rank
+    return synth.BASE_SEED + config + 1000 * rank
+
+
+def make_workload(args, rank):
+    """The synthetic batch of the chosen workload, and a one-line description."""
+    from paper_2604_06602_gb300 import synth
+    if args.workload == "c1":
+        b = synth.config1(seed=shard_seed(rank, 0))
+        return b, "one TESS-like 2-min curve x 18000 samples, W=361"
+    if args.workload == "c3":
+        b = synth.config3(seed=shard_seed(rank, 2), n_curves=args.curves or 4096)
+        return b, ("%d uneven curves: half TESS 2-min (N 5k-20k, W=361), half Kepler 29.4-min "
+                   "(N 4k-70k, W=25, 3-day gaps)" % b.B)
+    if args.workload == "c4":
+        b = synth.config4(seed=shard_seed(rank, 3), n_curves=args.curves or 256)
+        return b, "%d TESS 20-s curves x 118000 samples, W=2161, 1%% spikes" % b.B
+    b = synth.config2(seed=shard_seed(rank, 1), n_curves=args.curves or 1000, n=args.n)
+    return b, ("%d TESS-like 2-min curves x %d samples, W=361, alpha 2, c 5, 5 iters"
+               % (b.B, args.n))
 
 
 def window_work(flux, offsets, W, min_valid=None):
@@ -223,11 +244,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    from paper_2604_06602_gb300 import synth
-    batch = synth.config2(seed=shard_seed(0), n_curves=args.curves, n=args.n)
-    W = np.full(batch.B, oracle.window_length(batch.cadence[0]), np.int32)
+    batch, desc = make_workload(args, 0)
+    W = np.array([oracle.window_length(c) for c in batch.cadence], np.int32)
     threads = os.cpu_count() or 1
-    per_step = max(threads, 16)
+    per_step = min(batch.B, max(threads, 16) if args.workload != "c4" else max(2, threads // 4))
     idx_all = np.arange(batch.B)
     t_steps = []
     evals = 0
@@ -247,8 +267,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%d TESS-like curves x %d samples, W=361 (oracle: %d curves per step)"
-                               % (batch.B, args.n, per_step), "parallelism": "host threads"},
+        "config": {"workload": "%s (oracle: %d curves per step)" % (desc, per_step),
+                   "parallelism": "host threads"},
         "cpu_baseline": {"value": value, "unit": "window-evals/s", "cores": threads, "kind": "oracle",
                          "sample": "%d curves per step, FP64 C oracle" % per_step},
         "e2e": {"value": value, "unit": "window-evals/s", "h2d_bytes_per_step": 0,
@@ -274,7 +294,7 @@ def run_umi(args):
     barrier(dist)
     umi.load()
 
-    batch = synth.config2(seed=shard_seed(rank), n_curves=args.curves, n=args.n)
+    batch, desc = make_workload(args, rank)
     W = np.array([umi.window_length(c) for c in batch.cadence], np.int32)
     evals, samples = window_work(batch.flux, batch.offsets, W)
     flux = torch.from_numpy(batch.flux).to(dev)
@@ -288,9 +308,10 @@ def run_umi(args):
     # (outside the timed region, as a user would once per GPU).
     if args.tuning_file:
         umi.load_tuning(args.tuning_file)
-        tuned_plan = umi.get_plan(int(W[0]), -1)
     else:
-        tuned_plan, _ = umi.autotune(int(W[0]), positions=min(int(batch.flux.size), 4_000_000))
+        for w in sorted(set(W.tolist())):
+            umi.autotune(int(w), positions=min(int(batch.flux.size), 4_000_000))
+    tuned_plan = {int(w): umi.get_plan(int(w), -1) for w in sorted(set(W.tolist()))}
     if args.save_tuning and rank == 0:
         umi.save_tuning(args.save_tuning)
 
@@ -331,7 +352,7 @@ def run_umi(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = sms * LANES_PER_SM * sm_max * 1e6 / 1e12      # T lane-ops/s
     achieved = OPS_PER_SAMPLE * samples / (kernel_ms / 1e3) / 1e12
-    traffic = measured_traffic()
+    traffic = measured_traffic() if args.workload == "c2" and args.curves is None else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tlane-op/s",
                 "frac": achieved / peak_ops, "traffic": traffic,
                 "algorithmic_bytes": 12 * batch.flux.size,
@@ -344,9 +365,9 @@ def run_umi(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "%d TESS-like 2-min curves x %d samples, W=361, alpha 2, c 5, 5 iters, "
-                               "batched persistent kernel (CUDA graph)" % (batch.B, args.n),
-                   "global_batch": batch.B * world, "seq_len": args.n, "parallelism": "dp%d" % world,
+        "config": {"workload": desc + ", batched persistent kernel (CUDA graph)",
+                   "global_batch": batch.B * world, "seq_len": int(batch.lengths.max()),
+                   "parallelism": "dp%d" % world,
                    "l2": "flushed between steps (%d MB write)" % (flush.numel() * 4 >> 20),
                    "plan": tuned_plan},
         "curves_per_s": batch.B * world * args.steps / (elapsed_ms / 1e3),
@@ -359,7 +380,8 @@ def run_umi(args):
     if not args.no_extras and rank == 0:
         line["per_curve_launch"] = per_curve_leg(umi, torch, flux, batch, W, evals)
         line["e2e"] = e2e_leg(umi, torch, batch, W, evals, args)
-        line["serving"] = serving_leg(umi, torch, dev, args)
+        if args.workload == "c2":
+            line["serving"] = serving_leg(umi, torch, dev, args)
         line["cpu_baseline"] = cpu_baseline(batch, W)
     elif rank == 0:
         line["e2e"] = None
@@ -376,8 +398,8 @@ def per_curve_leg(umi, torch, flux, batch, W, evals):
     detr = torch.empty_like(flux)
     views = [(flux[batch.offsets[b]:batch.offsets[b + 1]], trend[batch.offsets[b]:batch.offsets[b + 1]],
               detr[batch.offsets[b]:batch.offsets[b + 1]]) for b in range(batch.B)]
-    for x, t, d in views[:8]:
-        umi.detrend(x, int(W[0]), trend=t, detr=d)
+    for b, (x, t, d) in enumerate(views[:8]):
+        umi.detrend(x, int(W[b]), trend=t, detr=d)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
