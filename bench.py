@@ -380,6 +380,7 @@ def run_umi(args):
     if not args.no_extras and rank == 0:
         line["per_curve_launch"] = per_curve_leg(umi, torch, flux, batch, W, evals)
         line["e2e"] = e2e_leg(umi, torch, batch, W, evals, args)
+        line["segmented"] = segmented_leg(umi, torch, flux, batch, W, evals)
         if args.workload == "c2":
             line["serving"] = serving_leg(umi, torch, dev, args)
         line["cpu_baseline"] = cpu_baseline(batch, W)
@@ -410,6 +411,25 @@ def per_curve_leg(umi, torch, flux, batch, W, evals):
     ms = e0.elapsed_time(e1)
     return {"value": evals / (ms / 1e3), "unit": "window-evals/s", "curves_per_s": batch.B / (ms / 1e3),
             "ms": ms, "launches": batch.B}
+
+
+def segmented_leg(umi, torch, flux, batch, W, evals):
+    """The same batch through umi_detrend_segmented (gap handling with the
+    default split rules): bit-pack kernel, host segment scan, one batched
+    launch per call."""
+    trend = torch.empty_like(flux)
+    detr = torch.empty_like(flux)
+    for _ in range(2):
+        _, _, kept = umi.detrend_segmented(flux, batch.offsets, W, trend=trend, detr=detr)
+    torch.cuda.synchronize()
+    steps = 5
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        umi.detrend_segmented(flux, batch.offsets, W, trend=trend, detr=detr)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": evals / dt, "unit": "window-evals/s", "ms_per_call": dt * 1e3,
+            "segments": kept, "curves_per_s": batch.B / dt}
 
 
 def e2e_leg(umi, torch, batch, W, evals, args):

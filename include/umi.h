@@ -176,6 +176,34 @@ umi_status umi_detrend_diag(const float *flux_d, int64_t n, int32_t W, const umi
                             float *trend_d, float *detr_d, float *median_d, int32_t *nvalid_d,
                             int32_t *nplus_d, float *scale_d, void *stream);
 
+/*
+ * Gap handling before the detrend (the pipeline step the paper lists before
+ * detrending, Table 3's caption; the W/3 minimum segment length of Section
+ * 4, Kepler Long-Cadence).  Each curve splits at every run of at least
+ * `gap_min` consecutive missing samples; leading and trailing missing runs
+ * belong to no segment; segments holding fewer than `min_seg` valid samples
+ * are dropped.  Kept segments are detrended as curves of their own, so no
+ * window reaches across a split; every other position gets NaN.
+ */
+typedef struct {
+    int64_t gap_min; /* missing-run length that splits a curve; <= 0 means W */
+    int64_t min_seg; /* minimum valid samples of a kept segment; < 0 means floor(W/3) */
+} umi_segment_params;
+
+void umi_default_segment_params(umi_segment_params *sp);
+
+/*
+ * umi_detrend_batched with gap handling.  Same buffers and layout; `seg`
+ * NULL means the defaults; `segments_out` (may be NULL) receives the number
+ * of kept segments.  The segment scan needs the validity of every sample on
+ * the host: the call enqueues a bit-packing kernel, copies 1 bit per sample
+ * back and synchronises `stream` before it enqueues the batched launch (the
+ * detrend itself stays asynchronous).  Scratch comes from cudaMallocAsync.
+ */
+umi_status umi_detrend_segmented(const float *flux_d, const int64_t *offsets_h, const int32_t *W_h,
+                                 int32_t B, const umi_params *params, const umi_segment_params *seg,
+                                 float *trend_d, float *detr_d, int64_t *segments_out, void *stream);
+
 /* Largest supported window length (odd). */
 int32_t umi_max_window(void);
 

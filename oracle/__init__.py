@@ -72,6 +72,10 @@ def _load():
             ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_int64, _f64p, _f64p, _f64p, _i32p,
             _i32p, _f64p]
         lib.umi_oracle_detrend_positions.restype = ctypes.c_int
+        lib.umi_oracle_detrend_segmented.argtypes = [
+            _f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+            ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _f64p, _f64p]
+        lib.umi_oracle_detrend_segmented.restype = ctypes.c_int
         lib.umi_oracle_detrend_batch.argtypes = [
             _f32p, _i64p, _i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
             ctypes.c_int, ctypes.c_int, _f64p, _f64p, ctypes.c_int]
@@ -135,6 +139,20 @@ def detrend_positions(flux, W, positions, alpha=2.0, c=5.0, iters=5, min_valid=-
     if rc != 0:
         raise ValueError("invalid oracle arguments")
     return out
+
+
+def detrend_segmented(flux, W, gap_min=0, min_seg=-1, alpha=2.0, c=5.0, iters=5, min_valid=-1):
+    """Gap-split detrend of one curve: segments end at runs of >= gap_min
+    missing samples (0 means W); segments with < min_seg valid samples (-1
+    means W // 3) are dropped.  Returns (trend, detr, kept_segments)."""
+    x = np.ascontiguousarray(flux, dtype=np.float32)
+    trend = np.empty(x.size, np.float64)
+    detr = np.empty(x.size, np.float64)
+    kept = _load().umi_oracle_detrend_segmented(x, x.size, int(W), float(alpha), float(c), int(iters),
+                                                int(min_valid), int(gap_min), int(min_seg), trend, detr)
+    if kept < 0:
+        raise ValueError("invalid oracle arguments")
+    return trend, detr, kept
 
 
 def detrend_batch(flux, offsets, W, alpha=2.0, c=5.0, iters=5, min_valid=-1, nthreads=None):

@@ -253,6 +253,63 @@ int umi_oracle_detrend_positions(const float *x, int64_t n, int32_t W, double al
     return 0;
 }
 
+/*
+ * Gap handling before the detrend (the pipeline step the paper lists before
+ * detrending in Table 3's caption; the W/3 minimum segment length of
+ * Section 4, Kepler Long-Cadence).  Reading: a curve splits into segments at
+ * every run of at least `gap_min` consecutive missing samples (default W);
+ * leading and trailing missing runs belong to no segment.  A segment holding
+ * fewer than `min_seg` valid samples (default floor(W/3)) is dropped.  Each
+ * kept segment is detrended on its own, so windows are truncated at segment
+ * ends exactly as at curve ends.  Positions outside kept segments get NaN.
+ * Returns the number of kept segments, or -1 on invalid arguments.
+ */
+int umi_oracle_detrend_segmented(const float *x, int64_t n, int32_t W, double alpha, double c,
+                                 int iters, int min_valid, int64_t gap_min, int64_t min_seg,
+                                 double *trend, double *detr)
+{
+    if (bad_args(n, W, alpha, c, iters))
+        return -1;
+    if (gap_min <= 0)
+        gap_min = W;
+    if (min_seg < 0)
+        min_seg = W / 3;
+    for (int64_t j = 0; j < n; ++j) {
+        trend[j] = NAN;
+        detr[j] = NAN;
+    }
+    int kept = 0;
+    int64_t j = 0;
+    while (j < n) {
+        /* Skip missing samples to the next segment start. */
+        while (j < n && !isfinite((double)x[j]))
+            ++j;
+        if (j >= n)
+            break;
+        int64_t start = j, last_valid = j, valid = 0;
+        int64_t run = 0; /* current run of missing samples */
+        while (j < n) {
+            if (isfinite((double)x[j])) {
+                run = 0;
+                last_valid = j;
+                ++valid;
+            } else if (++run >= gap_min) {
+                break;
+            }
+            ++j;
+        }
+        int64_t len = last_valid + 1 - start;
+        if (valid >= 1 && valid >= min_seg) {
+            if (umi_oracle_detrend(x + start, len, W, alpha, c, iters, min_valid, trend + start,
+                                   detr + start, NULL, NULL, NULL, NULL) != 0)
+                return -1;
+            ++kept;
+        }
+        j = last_valid + 1;
+    }
+    return kept;
+}
+
 /* ---- many curves in CSR layout, one curve per task, over pthreads -------- */
 typedef struct {
     const float *x;

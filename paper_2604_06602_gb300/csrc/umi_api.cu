@@ -508,6 +508,8 @@ static umi_status build_graph(const std::vector<Curve> &curves, GraphEntry *g)
 
 static std::atomic<long long> g_kernel_launches{0};
 
+void count_launches(int n) { g_kernel_launches += n; }
+
 static umi_status batched_impl(const float *flux, const int64_t *offsets, const int32_t *W,
                                int32_t B, const umi_params *params, float *trend, float *detr,
                                cudaStream_t stream, bool allow_graph)

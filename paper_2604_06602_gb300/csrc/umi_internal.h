@@ -57,6 +57,14 @@ int persistent_grid(const Plan &plan, bool diag);
 umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream,
                               int *launches);
 
+// Adds to the process-wide count of kernels launched by libumi.
+void count_launches(int n);
+
+// Gap-split detrend (umi_segments.cu).
+umi_status detrend_segmented(const float *flux, const int64_t *offsets, const int32_t *W, int32_t B,
+                             const umi_params *params, const umi_segment_params *seg, float *trend,
+                             float *detr, int64_t *segments_out, cudaStream_t stream);
+
 // Work-item list and per-variant launch layout for a curve table.
 struct BatchLayout {
     struct Band {

@@ -40,7 +40,8 @@ EXPORTS = [
     "umi_set_graph_cache", "umi_server_default_config", "umi_server_create", "umi_server_submit",
     "umi_server_poll", "umi_server_wait", "umi_server_copy_out", "umi_server_release",
     "umi_server_get_stats", "umi_server_inject_fault", "umi_server_destroy", "umi_last_error",
-    "umi_version", "umi_kernel_launch_count",
+    "umi_version", "umi_kernel_launch_count", "umi_default_segment_params",
+    "umi_detrend_segmented",
 ]
 
 
@@ -61,6 +62,10 @@ class Plan(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SegmentParams(ctypes.Structure):
+    _fields_ = [("gap_min", ctypes.c_int64), ("min_seg", ctypes.c_int64)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -135,6 +140,9 @@ def load(build_if_missing: bool = False):
             "umi_last_error": (ctypes.c_char_p, []),
             "umi_version": (ctypes.c_char_p, []),
             "umi_kernel_launch_count": (ctypes.c_longlong, []),
+            "umi_default_segment_params": (None, [P(SegmentParams)]),
+            "umi_detrend_segmented": (ctypes.c_int, [_vp, _vp, _vp, _i32, P(Params), P(SegmentParams),
+                                                     _vp, _vp, P(ctypes.c_int64), _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -273,6 +281,27 @@ def detrend_batched_noalloc(flux, offsets, W, p: Params | None = None, trend=Non
                                               _dev_f32(trend, "trend"), _dev_f32(detr, "detr"),
                                               _stream_handle(stream)))
     return trend, detr
+
+
+def detrend_segmented(flux, offsets, W, p: Params | None = None, gap_min=0, min_seg=-1, trend=None,
+                      detr=None, stream=None):
+    """CSR batch with gap handling (umi_detrend_segmented).  Returns
+    (trend, detr, kept_segments).  Synchronises the stream once (segment scan)."""
+    import torch
+    off, offp = _host_i64(offsets)
+    w, wp = _host_i32(W)
+    B = off.size - 1
+    if w.size != B:
+        raise ValueError("W must have one entry per curve")
+    trend = torch.empty_like(flux) if trend is None else trend
+    detr = torch.empty_like(flux) if detr is None else detr
+    sp = SegmentParams(int(gap_min), int(min_seg))
+    kept = ctypes.c_int64()
+    _check(load().umi_detrend_segmented(_dev_f32(flux, "flux"), offp, wp, B,
+                                        None if p is None else ctypes.byref(p), ctypes.byref(sp),
+                                        _dev_f32(trend, "trend"), _dev_f32(detr, "detr"),
+                                        ctypes.byref(kept), _stream_handle(stream)))
+    return trend, detr, kept.value
 
 
 def detrend_batched_host(flux, offsets, W, p: Params | None = None, trend=None, detr=None,

@@ -317,3 +317,74 @@ def test_bias_shape_matches_paper():
     assert 0.5 * abs(bias["alpha2_c5"]) < abs(off["a2"]) < 1.5 * abs(bias["alpha2_c5"])
     ratio = off["a10"] / off["a2"]
     assert ratio == pytest.approx(bias["alpha10_c2p5"] / bias["alpha2_c5"], rel=0.10)
+
+
+# ---- gap handling (Table 3's pipeline step; W/3 rule of Section 4) ----
+
+def _brute_segments(x, gap_min, min_seg):
+    """Segments as maximal runs between missing runs of length >= gap_min,
+    found on the validity string with a regular expression."""
+    import re
+    s = "".join("1" if np.isfinite(v) else "0" for v in x)
+    out = []
+    for m in re.finditer(r"1(?:0{0,%d}1)*" % (gap_min - 1), s):
+        valid = m.group(0).count("1")
+        if valid >= max(1, min_seg):
+            out.append((m.start(), m.end()))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_segments_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 300))
+    W = int(rng.choice([3, 7, 15, 31]))
+    x = synth.random_curve(seed, n)
+    for _ in range(int(rng.integers(0, 6))):
+        s0 = int(rng.integers(0, n))
+        x[s0:s0 + int(rng.integers(1, 3 * W))] = np.nan
+    x[rng.uniform(size=n) < 0.05] = np.nan
+    gap_min = int(rng.choice([1, 2, W // 2 + 1, W]))
+    min_seg = int(rng.choice([0, 3, W // 3, W]))
+    tr, de, kept = oracle.detrend_segmented(x, W, gap_min=gap_min, min_seg=min_seg)
+    segs = _brute_segments(x, gap_min, min_seg)
+    assert kept == len(segs)
+    covered = np.zeros(n, bool)
+    for a, b in segs:
+        covered[a:b] = True
+        ref = oracle.detrend(x[a:b], W)["trend"]          # each segment on its own
+        np.testing.assert_array_equal(tr[a:b], ref)
+    assert np.all(np.isnan(tr[~covered]))
+
+
+def test_segments_without_splits_equal_plain():
+    """No gap reaches gap_min and nothing is dropped: plain detrend."""
+    x = synth.random_curve(3, 2000, nan_frac=0.05, nan_runs=4, run_len=(1, 40))
+    tr, _, kept = oracle.detrend_segmented(x, 61, gap_min=10 ** 6, min_seg=0)
+    assert kept == 1
+    np.testing.assert_array_equal(tr, oracle.detrend(x, 61)["trend"])
+
+
+def test_long_gaps_only_drop_short_segments():
+    """A gap of at least W samples already separates the windows on both
+    sides, so splitting there changes nothing except dropping segments with
+    fewer than min_seg valid samples.  (With the defaults min_seg equals the
+    per-window minimum W/3, so such islands are NaN either way; a larger
+    min_seg shows the drop.)"""
+    W = 61
+    x = synth.random_curve(5, 3000)
+    x[1000:1000 + W] = np.nan
+    x[1500:1500 + 2 * W] = np.nan
+    x[2500:2500 + W] = np.nan
+    x[2500 + W + 30:2500 + 2 * W + 30] = np.nan   # a 30-sample island
+    island = slice(2500 + W, 2500 + W + 30)
+    plain = oracle.detrend(x, W)["trend"]
+    assert not np.any(np.isnan(plain[island]))    # 30 >= W // 3
+    tr, _, _ = oracle.detrend_segmented(x, W)     # gap_min = W, min_seg = W // 3
+    np.testing.assert_array_equal(tr, plain)
+    tr, _, kept = oracle.detrend_segmented(x, W, min_seg=W)
+    assert kept == 4                              # five segments, the island dropped
+    assert np.all(np.isnan(tr[island]))
+    keep = np.ones(x.size, bool)
+    keep[island] = False
+    np.testing.assert_array_equal(tr[keep], plain[keep])
