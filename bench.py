@@ -381,6 +381,7 @@ def run_umi(args):
         line["per_curve_launch"] = per_curve_leg(umi, torch, flux, batch, W, evals)
         line["e2e"] = e2e_leg(umi, torch, batch, W, evals, args)
         line["segmented"] = segmented_leg(umi, torch, flux, batch, W, evals)
+        line["mad_biweight"] = mad_leg(umi, torch, flux, batch, W, evals)
         if args.workload == "c2":
             line["serving"] = serving_leg(umi, torch, dev, args)
         line["cpu_baseline"] = cpu_baseline(batch, W)
@@ -411,6 +412,28 @@ def per_curve_leg(umi, torch, flux, batch, W, evals):
     ms = e0.elapsed_time(e1)
     return {"value": evals / (ms / 1e3), "unit": "window-evals/s", "curves_per_s": batch.B / (ms / 1e3),
             "ms": ms, "launches": batch.B}
+
+
+def mad_leg(umi, torch, flux, batch, W, evals):
+    """The paper's comparison estimator on the same batch: symmetric
+    biweight (alpha 1) with the MAD scale, which needs a second exact
+    selection per window."""
+    p = umi.params(alpha=1.0, scale_mode=umi.SCALE_MAD)
+    trend = torch.empty_like(flux)
+    detr = torch.empty_like(flux)
+    for _ in range(2):
+        umi.detrend_batched(flux, batch.offsets, W, p, trend=trend, detr=detr)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 5
+    e0.record()
+    for _ in range(steps):
+        umi.detrend_batched(flux, batch.offsets, W, p, trend=trend, detr=detr)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": evals / (ms / 1e3), "unit": "window-evals/s", "kernel_ms": ms,
+            "params": "alpha 1, c 5, MAD scale"}
 
 
 def segmented_leg(umi, torch, flux, batch, W, evals):

@@ -9,7 +9,8 @@
  *              of the curve; non-finite samples are missing and are dropped;
  *     Phase 1  m = exact median of the valid window samples (Section 2.1);
  *              for an even count the lower median, rank floor((n_valid-1)/2);
- *     Phase 2  s = 0.6745 * sqrt(mean over x > m of (x - m)^2)  (Eq. 1);
+ *     Phase 2  s = 0.6745 * sqrt(mean over x > m of (x - m)^2)  (Eq. 1), or
+ *              the MAD median |x - m| when params->scale_mode is UMI_SCALE_MAD;
  *     Phase 3  mu = m, then `iters` times: u = (x - mu)/(c s),
  *              u_eff = alpha u if u < 0 else u (Eq. 2),
  *              w = (1 - u_eff^2)^2 if |u_eff| < 1 else 0 (Eq. 3),
@@ -69,9 +70,19 @@ typedef struct {
     int32_t min_valid; /* minimum valid samples per window for an output; -1 means
                           floor(W/3) (the W/3 rule of Section 4, Kepler Long-Cadence);
                           0 disables the check */
+    int32_t scale_mode; /* UMI_SCALE_UPPER_RMS (0, the method: Eq. 1) or UMI_SCALE_MAD
+                           (1: s = median |x - m| over the window, the standard MAD the
+                           paper compares against in Sections 1, 2.2 and 3.1; alpha = 1
+                           with the MAD is the usual symmetric biweight).  The MAD mode
+                           runs one more exact selection per window and is several times
+                           slower. */
 } umi_params;
 
-/* Fill `p` with alpha 2, c 5, iters 5, min_valid -1.  NULL is ignored. */
+#define UMI_SCALE_UPPER_RMS 0
+#define UMI_SCALE_MAD 1
+
+/* Fill `p` with alpha 2, c 5, iters 5, min_valid -1, upper-RMS scale.  NULL
+ * is ignored. */
 void umi_default_params(umi_params *p);
 
 /*

@@ -67,6 +67,15 @@ def _load():
             _f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
             ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p, _i32p, _i32p, _f64p]
         lib.umi_oracle_detrend.restype = ctypes.c_int
+        lib.umi_oracle_window_estimate_mode.argtypes = [
+            _f64p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.umi_oracle_window_estimate_mode.restype = ctypes.c_int
+        lib.umi_oracle_detrend_mode.argtypes = [
+            _f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p, _i32p, _i32p, _f64p]
+        lib.umi_oracle_detrend_mode.restype = ctypes.c_int
         lib.umi_oracle_detrend_positions.argtypes = [
             _f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
             ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_int64, _f64p, _f64p, _f64p, _i32p,
@@ -94,32 +103,37 @@ def weight(u: float, alpha: float) -> float:
     return float(_load().umi_oracle_weight(float(u), float(alpha)))
 
 
-def window_estimate(values, alpha=2.0, c=5.0, iters=5):
+SCALE_UPPER_RMS = 0
+SCALE_MAD = 1
+
+
+def window_estimate(values, alpha=2.0, c=5.0, iters=5, scale_mode=SCALE_UPPER_RMS):
     """One window given as its valid samples.
 
-    Returns (median, n_plus, s, mu) after Phases 1-3 of Section 2.
+    Returns (median, n_plus, s, mu) after Phases 1-3 of Section 2; scale_mode
+    1 uses the MAD instead of the upper-RMS scale.
     """
     v = np.array(values, dtype=np.float64).ravel().copy()
     m, s, mu = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     npl = ctypes.c_int()
-    rc = _load().umi_oracle_window_estimate(v, int(v.size), float(alpha), float(c), int(iters),
-                                            ctypes.byref(m), ctypes.byref(npl),
-                                            ctypes.byref(s), ctypes.byref(mu))
+    rc = _load().umi_oracle_window_estimate_mode(v, int(v.size), float(alpha), float(c), int(iters),
+                                                 int(scale_mode), ctypes.byref(m), ctypes.byref(npl),
+                                                 ctypes.byref(s), ctypes.byref(mu))
     if rc != 0:
         raise ValueError("window_estimate needs at least one value")
     return m.value, npl.value, s.value, mu.value
 
 
-def detrend(flux, W, alpha=2.0, c=5.0, iters=5, min_valid=-1):
+def detrend(flux, W, alpha=2.0, c=5.0, iters=5, min_valid=-1, scale_mode=SCALE_UPPER_RMS):
     """Whole curve.  Returns a dict of float64/int32 arrays:
     trend, detr, median, nvalid, nplus, scale (see umi_oracle.c)."""
     x = np.ascontiguousarray(flux, dtype=np.float32)
     n = x.size
     out = {k: np.empty(n, np.float64) for k in ("trend", "detr", "median", "scale")}
     out.update({k: np.empty(n, np.int32) for k in ("nvalid", "nplus")})
-    rc = _load().umi_oracle_detrend(x, n, int(W), float(alpha), float(c), int(iters),
-                                    int(min_valid), out["trend"], out["detr"], out["median"],
-                                    out["nvalid"], out["nplus"], out["scale"])
+    rc = _load().umi_oracle_detrend_mode(x, n, int(W), float(alpha), float(c), int(iters),
+                                         int(min_valid), int(scale_mode), out["trend"], out["detr"],
+                                         out["median"], out["nvalid"], out["nplus"], out["scale"])
     if rc != 0:
         raise ValueError("invalid oracle arguments")
     return out

@@ -79,15 +79,23 @@ static int cmp_double(const void *a, const void *b)
     return (x > y) - (x < y);
 }
 
+/* Scale estimators: Eq. 1 (the method) and the MAD it is compared with. */
+enum { ORACLE_SCALE_UPPER_RMS = 0, ORACLE_SCALE_MAD = 1 };
+
 /*
  * One window, given as the multiset of its valid samples v[0..n) (all finite).
  * The array is sorted in place.  Writes the median (Phase 1), the count of
- * samples strictly above it, the scale s (Phase 2) and the location after
- * `iters` iterations of Phase 3.  Returns 0, or -1 when n < 1.
+ * samples strictly above it, the scale s and the location after `iters`
+ * iterations of Phase 3.  scale_mode 0 is the upper-RMS scale of Eq. 1
+ * (Section 2.2); scale_mode 1 is the standard MAD the paper compares it with
+ * (Sections 1 and 2.2, and the ablation of Section 3.1): the median of
+ * |v - m|, taken as the same lower-median order statistic, without a factor
+ * (the MAD is the convention 0.6745 * sigma_up is matched to).
+ * Returns 0, or -1 when n < 1.
  */
-int umi_oracle_window_estimate(double *v, int n, double alpha, double c, int iters,
-                               double *median_out, int *nplus_out, double *scale_out,
-                               double *mu_out)
+int umi_oracle_window_estimate_mode(double *v, int n, double alpha, double c, int iters,
+                                    int scale_mode, double *median_out, int *nplus_out,
+                                    double *scale_out, double *mu_out)
 {
     if (n < 1)
         return -1;
@@ -106,12 +114,23 @@ int umi_oracle_window_estimate(double *v, int n, double alpha, double c, int ite
         }
     }
     double s = 0.0;
-    if (nplus > 0)
+    if (scale_mode == ORACLE_SCALE_MAD) {
+        double *dev = (double *)malloc(sizeof(double) * (size_t)n);
+        if (!dev)
+            return -1;
+        for (int i = 0; i < n; ++i)
+            dev[i] = fabs(v[i] - m);
+        qsort(dev, (size_t)n, sizeof(double), cmp_double);
+        s = dev[(n - 1) / 2];
+        free(dev);
+    } else if (nplus > 0) {
         s = ORACLE_SCALE_FACTOR * sqrt(s2 / (double)nplus);
+    }
 
-    /* Phase 3 (Section 2.3, Eqs. 2-4): fixed number of reweighting steps. */
+    /* Phase 3 (Section 2.3, Eqs. 2-4): fixed number of reweighting steps.
+     * With the upper-RMS scale n_plus = 0 means s = 0; both give the median. */
     double mu = m;
-    if (nplus > 0 && s > 0.0) {
+    if (s > 0.0) {
         double cs = c * s;
         for (int it = 0; it < iters; ++it) {
             double sw = 0.0, swx = 0.0;
@@ -136,6 +155,14 @@ int umi_oracle_window_estimate(double *v, int n, double alpha, double c, int ite
     return 0;
 }
 
+int umi_oracle_window_estimate(double *v, int n, double alpha, double c, int iters,
+                               double *median_out, int *nplus_out, double *scale_out,
+                               double *mu_out)
+{
+    return umi_oracle_window_estimate_mode(v, n, alpha, c, iters, ORACLE_SCALE_UPPER_RMS,
+                                           median_out, nplus_out, scale_out, mu_out);
+}
+
 /* Everything the oracle reports for one output position. */
 typedef struct {
     double trend, detr, median, scale;
@@ -154,8 +181,8 @@ typedef struct {
  *   scale         s of Phase 2 where the trend is produced, else NaN.
  */
 static position_result oracle_position(const float *x, int64_t n, int32_t W, double alpha,
-                                       double c, int iters, int min_valid, int64_t j,
-                                       double *scratch)
+                                       double c, int iters, int min_valid, int scale_mode,
+                                       int64_t j, double *scratch)
 {
     int64_t h = (W - 1) / 2;
     int64_t lo = j - h < 0 ? 0 : j - h;
@@ -169,7 +196,8 @@ static position_result oracle_position(const float *x, int64_t n, int32_t W, dou
     double m = NAN, s = NAN, mu = NAN;
     int np = 0;
     if (cnt >= 1)
-        umi_oracle_window_estimate(scratch, cnt, alpha, c, iters, &m, &np, &s, &mu);
+        umi_oracle_window_estimate_mode(scratch, cnt, alpha, c, iters, scale_mode, &m, &np, &s,
+                                        &mu);
     int produce = cnt >= 1 && cnt >= min_valid && isfinite((double)x[j]);
     position_result r;
     r.trend = produce ? mu : NAN;
@@ -197,11 +225,11 @@ static int bad_args(int64_t n, int32_t W, double alpha, double c, int iters)
  * -1 on an invalid argument (W not odd or < 1, n < 0, iters < 0, alpha or c
  * not a positive finite number).
  */
-int umi_oracle_detrend(const float *x, int64_t n, int32_t W, double alpha, double c, int iters,
-                       int min_valid, double *trend, double *detr, double *median,
-                       int32_t *nvalid, int32_t *nplus, double *scale)
+int umi_oracle_detrend_mode(const float *x, int64_t n, int32_t W, double alpha, double c,
+                            int iters, int min_valid, int scale_mode, double *trend, double *detr,
+                            double *median, int32_t *nvalid, int32_t *nplus, double *scale)
 {
-    if (bad_args(n, W, alpha, c, iters))
+    if (bad_args(n, W, alpha, c, iters) || scale_mode < 0 || scale_mode > 1)
         return -1;
     if (n == 0)
         return 0;
@@ -210,7 +238,7 @@ int umi_oracle_detrend(const float *x, int64_t n, int32_t W, double alpha, doubl
         return -1;
     int mv = resolve_min_valid(W, min_valid);
     for (int64_t j = 0; j < n; ++j) {
-        position_result r = oracle_position(x, n, W, alpha, c, iters, mv, j, scratch);
+        position_result r = oracle_position(x, n, W, alpha, c, iters, mv, scale_mode, j, scratch);
         if (trend) trend[j] = r.trend;
         if (detr) detr[j] = r.detr;
         if (median) median[j] = r.median;
@@ -220,6 +248,14 @@ int umi_oracle_detrend(const float *x, int64_t n, int32_t W, double alpha, doubl
     }
     free(scratch);
     return 0;
+}
+
+int umi_oracle_detrend(const float *x, int64_t n, int32_t W, double alpha, double c, int iters,
+                       int min_valid, double *trend, double *detr, double *median,
+                       int32_t *nvalid, int32_t *nplus, double *scale)
+{
+    return umi_oracle_detrend_mode(x, n, W, alpha, c, iters, min_valid, ORACLE_SCALE_UPPER_RMS,
+                                   trend, detr, median, nvalid, nplus, scale);
 }
 
 /*
@@ -241,7 +277,8 @@ int umi_oracle_detrend_positions(const float *x, int64_t n, int32_t W, double al
         return -1;
     int mv = resolve_min_valid(W, min_valid);
     for (int64_t q = 0; q < count; ++q) {
-        position_result r = oracle_position(x, n, W, alpha, c, iters, mv, positions[q], scratch);
+        position_result r =
+            oracle_position(x, n, W, alpha, c, iters, mv, ORACLE_SCALE_UPPER_RMS, positions[q], scratch);
         if (trend) trend[q] = r.trend;
         if (detr) detr[q] = r.detr;
         if (median) median[q] = r.median;

@@ -179,13 +179,15 @@ umi_status check_params(const umi_params *p, umi_params *out)
         return fail(UMI_ERR_INVALID_ARG, "c must be a positive finite number");
     if (q.iters < 0 || q.iters > 1000) return fail(UMI_ERR_INVALID_ARG, "iters must be in [0, 1000]");
     if (q.min_valid < -1) return fail(UMI_ERR_INVALID_ARG, "min_valid must be >= -1");
+    if (q.scale_mode != UMI_SCALE_UPPER_RMS && q.scale_mode != UMI_SCALE_MAD)
+        return fail(UMI_ERR_INVALID_ARG, "scale_mode must be UMI_SCALE_UPPER_RMS or UMI_SCALE_MAD");
     *out = q;
     return UMI_OK;
 }
 
 static std::mutex g_attr_mu;
 
-umi_status prepare_kernel(const Plan &plan, bool diag)
+umi_status prepare_kernel(const Plan &plan, int flavour)
 {
     int n = 0;
     const Variant *t = variant_table(&n);
@@ -196,18 +198,18 @@ umi_status prepare_kernel(const Plan &plan, bool diag)
         return fail(UMI_ERR_INVALID_ARG, "tile needs more shared memory than the device allows");
     if (smem > 48 * 1024) {
         std::lock_guard<std::mutex> lk(g_attr_mu);
-        const void *k = diag ? t[plan.variant].kernel_diag : t[plan.variant].kernel;
+        const void *k = t[plan.variant].kernel[flavour];
         UMI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                  "cudaFuncSetAttribute");
     }
     return UMI_OK;
 }
 
-int persistent_grid(const Plan &plan, bool diag)
+int persistent_grid(const Plan &plan, int flavour)
 {
     int n = 0;
     const Variant *t = variant_table(&n);
-    const void *k = diag ? t[plan.variant].kernel_diag : t[plan.variant].kernel;
+    const void *k = t[plan.variant].kernel[flavour];
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, plan.threads, plan.smem_bytes()) !=
             cudaSuccess ||
@@ -230,7 +232,7 @@ static Curve make_curve(const float *flux, float *trend, float *detr, int64_t n,
     c.alpha = p.alpha;
     c.c = p.c;
     c.iters = p.iters;
-    c.reserved = 0;
+    c.scale_mode = p.scale_mode;
     return c;
 }
 
@@ -250,8 +252,8 @@ static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const 
     Plan plan;
     st = make_plan(W, n, &plan);
     if (st != UMI_OK) return st;
-    const bool use_diag = diag != nullptr;
-    st = prepare_kernel(plan, use_diag);
+    const int flavour = (diag ? kFlagDiag : 0) | (p.scale_mode == UMI_SCALE_MAD ? kFlagMad : 0);
+    st = prepare_kernel(plan, flavour);
     if (st != UMI_OK) return st;
     const int64_t T = plan.tile();
     const int64_t items = (n + T - 1) / T;
@@ -267,7 +269,7 @@ static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const 
     if (diag) a.diag = *diag;
     int nv = 0;
     const Variant *t = variant_table(&nv);
-    LaunchFn fn = use_diag ? t[plan.variant].launch_diag : t[plan.variant].launch;
+    LaunchFn fn = t[plan.variant].launch[flavour];
     const int warps = plan.threads / 32;
     const int64_t grid = (items + warps - 1) / warps;
     cudaError_t e = fn(a, (int)grid, plan.threads, plan.smem_bytes(), stream);
@@ -282,13 +284,14 @@ umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout)
     variant_table(&nvar);
     // One band per distinct plan (variant, chain, threads), in descending
     // slot capacity so that the heaviest tiles start first.
-    std::map<std::tuple<int, int, int>, std::vector<int>> by_plan;
+    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> by_plan;
     std::vector<Plan> plans;
     for (size_t b = 0; b < curves.size(); ++b) {
         Plan p;
         umi_status st = make_plan(curves[b].W, -1, &p);
         if (st != UMI_OK) return st;
-        by_plan[std::make_tuple(-p.G * p.R, p.chain, p.threads)].push_back((int)b);
+        const int flavour = curves[b].scale_mode == UMI_SCALE_MAD ? kFlagMad : 0;
+        by_plan[std::make_tuple(-p.G * p.R, p.variant, p.chain, p.threads, flavour)].push_back((int)b);
         plans.push_back(p);
     }
     layout->bands.clear();
@@ -296,6 +299,7 @@ umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout)
     for (auto &kv : by_plan) {
         BatchLayout::Band band;
         band.plan = plans[kv.second.front()];
+        band.flavour = std::get<4>(kv.first);
         band.first_item = (int32_t)layout->items.size();
         const int64_t T = band.plan.tile();
         // Longest curves first: their tiles are interleaved with others by the
@@ -351,9 +355,10 @@ static umi_status enqueue_bands(const BatchLayout &lay, char *dev, const Scratch
         a.chain = band.plan.chain;
         a.queue = reinterpret_cast<int32_t *>(dev + sc.counter_off) + k;
         const int warps = band.plan.threads / 32;
-        const int grid = std::min((band.n_items + warps - 1) / warps, persistent_grid(band.plan, false));
-        cudaError_t e = t[band.plan.variant].launch(a, grid, band.plan.threads,
-                                                    band.plan.smem_bytes(), stream);
+        const int grid =
+            std::min((band.n_items + warps - 1) / warps, persistent_grid(band.plan, band.flavour));
+        cudaError_t e = t[band.plan.variant].launch[band.flavour](a, grid, band.plan.threads,
+                                                                  band.plan.smem_bytes(), stream);
         if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
         ++count;
     }
@@ -366,7 +371,7 @@ umi_status prepare_batch(const std::vector<Curve> &curves, PreparedBatch *pb)
     umi_status st = build_layout(curves, &pb->layout);
     if (st != UMI_OK) return st;
     for (const auto &band : pb->layout.bands) {
-        st = prepare_kernel(band.plan, false);
+        st = prepare_kernel(band.plan, band.flavour);
         if (st != UMI_OK) return st;
     }
     const Scratch sc = scratch_layout(curves.size(), pb->layout.items.size(), pb->layout.bands.size());
@@ -403,7 +408,7 @@ umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t str
     if (st != UMI_OK) return st;
     if (lay.items.empty()) return UMI_OK;
     for (const auto &band : lay.bands) {
-        st = prepare_kernel(band.plan, false);
+        st = prepare_kernel(band.plan, band.flavour);
         if (st != UMI_OK) return st;
     }
     const Scratch sc = scratch_layout(curves.size(), lay.items.size(), lay.bands.size());
@@ -474,7 +479,7 @@ static umi_status build_graph(const std::vector<Curve> &curves, GraphEntry *g)
     umi_status st = build_layout(curves, &lay);
     if (st != UMI_OK) return st;
     for (const auto &band : lay.bands) {
-        st = prepare_kernel(band.plan, false);
+        st = prepare_kernel(band.plan, band.flavour);
         if (st != UMI_OK) return st;
     }
     const Scratch sc = scratch_layout(curves.size(), lay.items.size(), lay.bands.size());
@@ -628,7 +633,7 @@ static umi_status time_plan(const Plan &plan, const float *flux, float *trend, f
     const int64_t tiles = (n + T - 1) / T;
     for (int64_t k = 0; k < tiles; ++k) lay.items.push_back(Item{0, (int32_t)k});
     lay.bands[0].n_items = (int32_t)tiles;
-    umi_status st = prepare_kernel(plan, false);
+    umi_status st = prepare_kernel(plan, 0);
     if (st != UMI_OK) return st;
     const Scratch sc = scratch_layout(1, lay.items.size(), 1);
     std::vector<char> host(sc.counter_off);
@@ -723,7 +728,7 @@ static umi_status noalloc_batched(const float *flux, const int64_t *offsets, con
                         std::to_string((size_t)UMI_NOALLOC_SCRATCH_BYTES) +
                         "-byte no-alloc scratch; split the batch");
     for (const auto &band : lay.bands) {
-        st = prepare_kernel(band.plan, false);
+        st = prepare_kernel(band.plan, band.flavour);
         if (st != UMI_OK) return st;
     }
     void *dev = nullptr;
@@ -756,6 +761,7 @@ void umi_default_params(umi_params *p)
     p->c = 5.0f;
     p->iters = 5;
     p->min_valid = -1;
+    p->scale_mode = UMI_SCALE_UPPER_RMS;
 }
 
 int32_t umi_window_length(double cadence_days, double window_days)

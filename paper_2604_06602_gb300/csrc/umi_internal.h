@@ -46,9 +46,10 @@ bool legal_chain(int G, int chain);
 umi_status make_plan(int W, int64_t positions, Plan *plan);
 umi_status check_params(const umi_params *p, umi_params *out);
 int resolve_min_valid(int W, int min_valid);
-umi_status prepare_kernel(const Plan &plan, bool diag);
+// `flavour` = kFlagDiag | kFlagMad bits (the kernel build to use).
+umi_status prepare_kernel(const Plan &plan, int flavour);
 // Persistent grid size for a plan on the current device.
-int persistent_grid(const Plan &plan, bool diag);
+int persistent_grid(const Plan &plan, int flavour);
 
 // One batched launch over an explicit curve table (used by the CSR entry
 // point and by the server).  `curves` are host descriptors with device data
@@ -69,6 +70,7 @@ umi_status detrend_segmented(const float *flux, const int64_t *offsets, const in
 struct BatchLayout {
     struct Band {
         Plan plan;
+        int flavour = 0;  // kFlagMad when the band's curves use the MAD scale
         int32_t first_item = 0;
         int32_t n_items = 0;
     };

@@ -55,7 +55,7 @@ struct Curve {
     float alpha;
     float c;
     int32_t iters;
-    int32_t reserved;
+    int32_t scale_mode;  // 0: upper-RMS scale (Eq. 1); 1: MAD
 };
 
 struct Diag {
@@ -199,7 +199,10 @@ struct MedianState {
     bool have;
 };
 
-template <int G, int R, bool DIAG>
+// Kernel flags: diagnostic outputs, MAD scale instead of Eq. 1.
+enum : int { kFlagDiag = 1, kFlagMad = 2 };
+
+template <int G, int R, int FLAGS>
 __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, const float *tile,
                                               int64_t t0, int q0, int P, int glane)
 {
@@ -368,6 +371,36 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             }
             const float s2sum = group_sum<G>(s2.x + s2.y);
             s = (st.Gp > 0) ? kScaleFactor * sqrtf(s2sum / (float)st.Gp) : 0.f;
+            if constexpr ((FLAGS & kFlagMad) != 0) {
+                // MAD = the order statistic of rank floor((nv-1)/2) of |y| over
+                // the valid slots, by bisection on the bit patterns of
+                // non-negative floats (their order as unsigned integers).
+                // Gap slots have |y| near 2^100 and sort above every candidate.
+                float hi = 0.f;
+#pragma unroll
+                for (int k = 0; k < R / 2; ++k) {
+                    const float a = fabsf(x[k].x), b = fabsf(x[k].y);
+                    hi = fmaxf(hi, a < 0x1p98f ? a : 0.f);
+                    hi = fmaxf(hi, b < 0x1p98f ? b : 0.f);
+                }
+                hi = group_max<G>(hi);
+                const unsigned hk = __float_as_uint(hi);
+                const int nbits = hk ? 32 - __clz((int)hk) : 0;
+                const int nb = (int)__reduce_max_sync(0xffffffffu, (unsigned)(produce ? nbits : 0));
+                const int target = (st.nv - 1) >> 1;
+                unsigned res = 0u;
+#pragma unroll 1
+                for (int b = nb - 1; b >= 0; --b) {
+                    const float cand = __uint_as_float(res | (1u << b));
+                    int c = 0;
+#pragma unroll
+                    for (int k = 0; k < R / 2; ++k)
+                        c += ((fabsf(x[k].x) < cand) ? 1 : 0) + ((fabsf(x[k].y) < cand) ? 1 : 0);
+                    c = group_sum_int<G>(c);
+                    if (c <= target) res |= (1u << b);
+                }
+                s = __uint_as_float(res);
+            }
             const bool iterate = produce && (s > 0.f);
             if (__any_sync(0xffffffffu, iterate)) {
                 // u_eff of Eq. 2 is min(y kp - delta kp, y kn - delta kn) with
@@ -412,7 +445,7 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             const float nanv = __int_as_float(0x7fc00000);
             cv.trend[p] = produce ? mu : nanv;
             cv.detr[p] = produce ? __fdiv_rn(centre, mu) : nanv;
-            if constexpr (DIAG) {
+            if constexpr ((FLAGS & kFlagDiag) != 0) {
                 if (dg.median) dg.median[p] = (st.nv >= 1) ? st.m : nanv;
                 if (dg.nvalid) dg.nvalid[p] = st.nv;
                 if (dg.nplus) dg.nplus[p] = (st.nv >= 1) ? st.Gp : 0;
@@ -427,8 +460,10 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
 // CTA-wide barrier is ever needed.  Without a queue, warp w of CTA b takes
 // item b*warps + w; with a queue, each warp pulls items until none is left.
 // Dynamic shared memory: warps * (T + S - 1) floats.  MINB (CTAs of 256
-// threads per SM) sets the register budget the compiler aims for.
-template <int G, int R, int MINB, bool DIAG>
+// threads per SM) sets the register budget the compiler aims for.  FLAGS
+// selects the diagnostic outputs and the MAD scale; every curve of one launch
+// must have the scale mode the kernel was built for.
+template <int G, int R, int MINB, int FLAGS>
 __global__ void __launch_bounds__(256, MINB) umi_tile_kernel(LaunchArgs a)
 {
     extern __shared__ float smem[];
@@ -466,7 +501,7 @@ __global__ void __launch_bounds__(256, MINB) umi_tile_kernel(LaunchArgs a)
             tile[k] = v;
         }
         __syncwarp();
-        process_chain<G, R, DIAG>(cv, a.diag, tile, t0, group * P, P, glane);
+        process_chain<G, R, FLAGS>(cv, a.diag, tile, t0, group * P, P, glane);
         __syncwarp();  // every lane is done with the tile before it is restaged
         if (!a.queue) break;
     }

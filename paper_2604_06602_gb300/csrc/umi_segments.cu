@@ -178,7 +178,7 @@ umi_status detrend_segmented(const float *flux, const int64_t *offsets, const in
             c.alpha = p.alpha;
             c.c = p.c;
             c.iters = p.iters;
-            c.reserved = 0;
+            c.scale_mode = p.scale_mode;
             curves.push_back(c);
         }
     }

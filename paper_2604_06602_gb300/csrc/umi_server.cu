@@ -299,7 +299,7 @@ static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mute
         c.alpha = j.p.alpha;
         c.c = j.p.c;
         c.iters = j.p.iters;
-        c.reserved = 0;
+        c.scale_mode = j.p.scale_mode;
         curves.push_back(c);
     }
     int launches = 0;

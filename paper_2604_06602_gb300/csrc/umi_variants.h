@@ -12,14 +12,15 @@ namespace umi {
 typedef cudaError_t (*LaunchFn)(const LaunchArgs &args, int grid, int threads, size_t smem,
                                 cudaStream_t stream);
 
+// Kernel flavours: index = kFlagDiag | kFlagMad bits.
+constexpr int kFlavours = 4;
+
 struct Variant {
     int G;
     int R;
     int minb;
-    LaunchFn launch;       // trend / detr only
-    LaunchFn launch_diag;  // with the diagnostic outputs
-    const void *kernel;    // for occupancy queries and attributes
-    const void *kernel_diag;
+    LaunchFn launch[kFlavours];
+    const void *kernel[kFlavours];  // for occupancy queries and attributes
 };
 
 // All compiled variants, ordered by slot capacity G*R (ascending).
@@ -31,36 +32,33 @@ const Variant *variant_table(int *count);
 #define UMI_VNAME(p, G_, R_, M_) p##G_##_##R_##_##M_
 #define UMI_DEFINE_VARIANT(G_, R_, M_)                                                        \
     namespace umi {                                                                           \
-    cudaError_t UMI_VNAME(launch_v, G_, R_, M_)(const LaunchArgs &a, int grid, int threads,  \
-                                                size_t smem, cudaStream_t st)                \
+    template <int F>                                                                          \
+    static cudaError_t UMI_VNAME(launch_, G_, R_, M_)(const LaunchArgs &a, int grid,          \
+                                                      int threads, size_t smem,               \
+                                                      cudaStream_t st)                        \
     {                                                                                         \
-        umi_tile_kernel<G_, R_, M_, false><<<grid, threads, smem, st>>>(a);                   \
+        umi_tile_kernel<G_, R_, M_, F><<<grid, threads, smem, st>>>(a);                       \
         return cudaGetLastError();                                                            \
     }                                                                                         \
-    cudaError_t UMI_VNAME(launch_d, G_, R_, M_)(const LaunchArgs &a, int grid, int threads,  \
-                                                size_t smem, cudaStream_t st)                \
+    void UMI_VNAME(fill_, G_, R_, M_)(Variant * v)                                            \
     {                                                                                         \
-        umi_tile_kernel<G_, R_, M_, true><<<grid, threads, smem, st>>>(a);                    \
-        return cudaGetLastError();                                                            \
-    }                                                                                         \
-    const void *UMI_VNAME(kernel_v, G_, R_, M_)()                                             \
-    {                                                                                         \
-        return (const void *)umi_tile_kernel<G_, R_, M_, false>;                              \
-    }                                                                                         \
-    const void *UMI_VNAME(kernel_d, G_, R_, M_)()                                             \
-    {                                                                                         \
-        return (const void *)umi_tile_kernel<G_, R_, M_, true>;                               \
+        v->G = G_;                                                                            \
+        v->R = R_;                                                                            \
+        v->minb = M_;                                                                         \
+        v->launch[0] = UMI_VNAME(launch_, G_, R_, M_)<0>;                                     \
+        v->launch[1] = UMI_VNAME(launch_, G_, R_, M_)<1>;                                     \
+        v->launch[2] = UMI_VNAME(launch_, G_, R_, M_)<2>;                                     \
+        v->launch[3] = UMI_VNAME(launch_, G_, R_, M_)<3>;                                     \
+        v->kernel[0] = (const void *)umi_tile_kernel<G_, R_, M_, 0>;                          \
+        v->kernel[1] = (const void *)umi_tile_kernel<G_, R_, M_, 1>;                          \
+        v->kernel[2] = (const void *)umi_tile_kernel<G_, R_, M_, 2>;                          \
+        v->kernel[3] = (const void *)umi_tile_kernel<G_, R_, M_, 3>;                          \
     }                                                                                         \
     }
 
-#define UMI_DECLARE_VARIANT(G_, R_, M_)                                                       \
-    namespace umi {                                                                           \
-    cudaError_t UMI_VNAME(launch_v, G_, R_, M_)(const LaunchArgs &, int, int, size_t,        \
-                                                cudaStream_t);                               \
-    cudaError_t UMI_VNAME(launch_d, G_, R_, M_)(const LaunchArgs &, int, int, size_t,        \
-                                                cudaStream_t);                               \
-    const void *UMI_VNAME(kernel_v, G_, R_, M_)();                                            \
-    const void *UMI_VNAME(kernel_d, G_, R_, M_)();                                            \
+#define UMI_DECLARE_VARIANT(G_, R_, M_)                   \
+    namespace umi {                                       \
+    void UMI_VNAME(fill_, G_, R_, M_)(Variant * v);       \
     }
 
 // The variant list: (G, R, MINB), ordered by slot capacity G*R; for equal

@@ -1,19 +1,28 @@
-// The compiled variant table (launchers are defined in umi_variants_*.cu).
+// The compiled variant table (kernels are defined in umi_variants_*.cu).
 #include "umi_variants.h"
 
 UMI_VARIANT_LIST(UMI_DECLARE_VARIANT)
 
 namespace umi {
 
+namespace {
+struct Table {
+    Variant v[64];
+    int n = 0;
+    Table()
+    {
+#define UMI_TABLE_ENTRY(G_, R_, M_) UMI_VNAME(fill_, G_, R_, M_)(&v[n++]);
+        UMI_VARIANT_LIST(UMI_TABLE_ENTRY)
+#undef UMI_TABLE_ENTRY
+    }
+};
+}  // namespace
+
 const Variant *variant_table(int *count)
 {
-#define UMI_TABLE_ENTRY(G_, R_, M_)                                                       \
-    {G_, R_, M_, UMI_VNAME(launch_v, G_, R_, M_), UMI_VNAME(launch_d, G_, R_, M_),         \
-     UMI_VNAME(kernel_v, G_, R_, M_)(), UMI_VNAME(kernel_d, G_, R_, M_)()},
-    static const Variant table[] = {UMI_VARIANT_LIST(UMI_TABLE_ENTRY)};
-#undef UMI_TABLE_ENTRY
-    if (count) *count = (int)(sizeof(table) / sizeof(table[0]));
-    return table;
+    static const Table table;
+    if (count) *count = table.n;
+    return table.v;
 }
 
 }  // namespace umi

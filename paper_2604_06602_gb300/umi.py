@@ -51,9 +51,13 @@ class UmiError(RuntimeError):
         self.status = status
 
 
+SCALE_UPPER_RMS = 0
+SCALE_MAD = 1
+
+
 class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_float), ("c", ctypes.c_float), ("iters", ctypes.c_int32),
-                ("min_valid", ctypes.c_int32)]
+                ("min_valid", ctypes.c_int32), ("scale_mode", ctypes.c_int32)]
 
 
 class Plan(ctypes.Structure):
@@ -159,8 +163,8 @@ def _check(status):
     return status
 
 
-def params(alpha=2.0, c=5.0, iters=5, min_valid=-1) -> Params:
-    return Params(float(alpha), float(c), int(iters), int(min_valid))
+def params(alpha=2.0, c=5.0, iters=5, min_valid=-1, scale_mode=SCALE_UPPER_RMS) -> Params:
+    return Params(float(alpha), float(c), int(iters), int(min_valid), int(scale_mode))
 
 
 def default_params() -> Params:

@@ -307,3 +307,37 @@ def test_graph_cache_follows_tuning_changes(umi, tmp_path):
         assert umi.kernel_launch_count() > launches0
     finally:
         umi.clear_tuning()
+
+
+@pytest.mark.parametrize("W", [25, 361, 2161])
+@pytest.mark.parametrize("alpha", [1.0, 2.0])
+def test_mad_scale_mode(umi, W, alpha):
+    """MAD scale (the comparison estimator; alpha 1 is the symmetric
+    biweight).  The GPU's MAD is the FP32 rounding of the exact MAD (|x - m|
+    is correctly rounded and rounding is monotone), so the scale agrees to one
+    FP32 ulp; the trend to 1e-5."""
+    n = 3 * tile_of(umi, W) + 11
+    x = synth.random_curve(77 + W, n, nan_runs=3, run_len=(1, W))
+    x[::41] -= 5e-3                                      # dips below the median
+    p = umi.params(alpha=alpha, scale_mode=umi.SCALE_MAD)
+    got = run_diag(umi, x, W, p)
+    ref = oracle.detrend(x, W, alpha=alpha, scale_mode=oracle.SCALE_MAD)
+    compare_diag(got, ref, what="MAD W=%d alpha=%g" % (W, alpha))
+    ok = ~np.isnan(ref["scale"])
+    np.testing.assert_allclose(got["scale"][ok], ref["scale"][ok], rtol=2 ** -23, atol=0)
+    # The same through the batched path.
+    xd = torch.from_numpy(x).cuda()
+    tr, _ = umi.detrend_batched(xd, np.array([0, n]), np.array([W], np.int32), p)
+    torch.cuda.synchronize()
+    assert np.array_equal(tr.cpu().numpy(), got["trend"], equal_nan=True)
+
+
+def test_mad_degenerate_and_ties(umi):
+    """Half the window on one value gives MAD 0 and the median as trend."""
+    x = np.ones(900, np.float32)
+    x[::3] = 1.5
+    x[1::7] = np.nan
+    p = umi.params(scale_mode=umi.SCALE_MAD)
+    got = run_diag(umi, x, 61, p)
+    ref = oracle.detrend(x, 61, scale_mode=oracle.SCALE_MAD)
+    compare_diag(got, ref, what="MAD ties")

@@ -388,3 +388,47 @@ def test_long_gaps_only_drop_short_segments():
     keep = np.ones(x.size, bool)
     keep[island] = False
     np.testing.assert_array_equal(tr[keep], plain[keep])
+
+
+# ---- MAD scale (the comparison scale of Sections 1, 2.2 and 3.1) ----
+
+def test_mad_closed_forms():
+    """MAD about the median: Exp(1) gives sinh(d) = 1/2, so d = asinh(1/2);
+    a Gaussian gives Phi^-1(3/4) sigma = 0.67449 sigma (the convention the
+    0.6745 of Eq. 1 is matched to)."""
+    v = np.random.default_rng(3).exponential(1.0, 400001)
+    assert oracle.window_estimate(v, scale_mode=oracle.SCALE_MAD)[2] == pytest.approx(
+        math.asinh(0.5), rel=0.015)
+    g = 2.0 + 3.0 * np.random.default_rng(4).normal(size=400001)
+    assert oracle.window_estimate(g, scale_mode=oracle.SCALE_MAD)[2] / 3.0 == pytest.approx(
+        0.674489750, rel=0.01)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mad_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 50))
+    x = (rng.integers(-5, 6, size=n) * 0.5).astype(np.float32)
+    x[rng.uniform(size=n) < 0.15] = np.nan
+    W = 9
+    out = oracle.detrend(x, W, min_valid=0, scale_mode=oracle.SCALE_MAD)
+    for j, vals in _brute_windows(x, W):
+        if not vals or not np.isfinite(x[j]):
+            continue
+        m = vals[(len(vals) - 1) // 2]
+        dev = sorted(abs(v - m) for v in vals)
+        assert out["scale"][j] == dev[(len(dev) - 1) // 2]
+
+
+def test_dips_inflate_mad_but_not_upper_rms():
+    """Section 2.2: transit-like dips below the median enter the MAD but not
+    the upper-RMS scale."""
+    rng = np.random.default_rng(12)
+    v = rng.normal(size=361)
+    m = np.median(v)
+    w = v.copy()
+    low = np.nonzero(v < m)[0][:60]
+    w[low] -= 10.0
+    assert oracle.window_estimate(w)[2] == oracle.window_estimate(v)[2]
+    assert oracle.window_estimate(w, scale_mode=oracle.SCALE_MAD)[2] > \
+        1.05 * oracle.window_estimate(v, scale_mode=oracle.SCALE_MAD)[2]
