@@ -71,11 +71,14 @@ def curve_rng(seed: int, index: int) -> np.random.Generator:
 
 
 def _trapezoid(t, depth, duration, period, epoch, ingress_frac=0.1):
-    """Periodic trapezoid dip profile (positive numbers = flux removed)."""
+    """Periodic trapezoid dip profile (positive numbers = flux removed);
+    ingress_frac = 0 gives a box."""
     if depth <= 0 or duration <= 0:
         return np.zeros_like(t)
     phase = np.mod(t - epoch + 0.5 * period, period) - 0.5 * period
     half = 0.5 * duration
+    if ingress_frac <= 0:
+        return depth * (np.abs(phase) <= half)
     tau = ingress_frac * duration
     frac = np.clip((half - np.abs(phase)) / tau, 0.0, 1.0)
     return depth * frac
@@ -262,6 +265,48 @@ def serving_requests(seed: int = BASE_SEED + 4, n_requests: int = 200000, rate_h
             pool.append(f); cads.append(CADENCE_TESS_20S); kinds.append("tess20s")
     which = rng.integers(0, max_distinct, size=n_requests)
     return arrivals, pool, which, np.asarray(cads), kinds
+
+
+def injection_base(seed, n_stars, mission="tess"):
+    """Noise-and-variability curves for box-transit injection (stand-ins for
+    the TESS sector-6 / Kepler Q5 stars of Section 3.2).  TESS: 2-min cadence,
+    18,000 samples, white noise log-U(500, 2000) ppm, AR(1) red noise at 30 %
+    of it, 0-2 sinusoids of up to 2 sigma, the 1-day mid gap.  Kepler: 29.4-min
+    cadence, 4,400 samples (one quarter), white noise log-U(50, 200) ppm, the
+    same red-noise and variability recipe, no gap.  Returns (batch without
+    transits, box-transit unit profiles: 1 inside a transit, P = 3 d,
+    D = 3 h, random epoch)."""
+    kepler = mission == "kepler"
+    cad = CADENCE_KEPLER_LC if kepler else CADENCE_TESS_2MIN
+    n = 4400 if kepler else 18000
+    lo, hi = (5e-5, 2e-4) if kepler else (5e-4, 2e-3)
+    curves, profiles, ep = [], [], []
+    for b in range(n_stars):
+        rng = curve_rng(seed, b)
+        sigma = _loguniform(rng, lo, hi)
+        f, _, e = make_curve(rng, n, cad, sigma=sigma, depth=0.0, n_sines=int(rng.integers(0, 3)),
+                             sine_amp=float(rng.uniform(0.0, 2.0)) * sigma, red_phi=0.99,
+                             red_sigma=0.3 * sigma, n_flares=0,
+                             mid_gap_days=0.0 if kepler else 1.0)
+        t = np.arange(n) * cad
+        epoch = rng.uniform(0.0, 3.0)
+        profiles.append(_trapezoid(t, 1.0, 3.0 / 24.0, 3.0, epoch, ingress_frac=0.0).astype(np.float32))
+        curves.append((f, np.zeros(n, np.float32)))
+        ep.append(epoch)
+    batch = _assemble(curves, [cad] * n_stars, [0.0] * n_stars, [3.0] * n_stars, [3.0] * n_stars, ep,
+                      "%s-injection-%d" % (mission, n_stars))
+    return batch, np.concatenate(profiles)
+
+
+def inject(base, unit_profile, depth):
+    """Copy of `base` with box transits of the given fractional depth."""
+    b = CurveBatch(base.flux - np.float32(depth) * unit_profile, base.offsets.copy(), base.cadence.copy(),
+                   (np.float32(depth) * unit_profile).astype(np.float32),
+                   np.full(base.B, depth, np.float64), base.duration_d.copy(), base.period_d.copy(),
+                   base.epoch_d.copy(), base.window_days, base.name + "+%gppm" % (depth * 1e6),
+                   dict(base.meta))
+    b.flux = b.flux.astype(np.float32)
+    return b
 
 
 def random_curve(seed, n, *, nan_frac=0.0, nan_runs=0, run_len=(1, 50), ties=False,

@@ -64,29 +64,7 @@ def compare_detr(dgot, dref, what=""):
 
 
 def depth_recovery_errors(detr, batch, idx=None):
-    """Median-free per-curve depth recovery error (percent).
-
-    Reading of the paper's metric (Section 3.2 aggregates each star's
-    absolute percentage depth error by a median over stars): recovered depth = median of detrended flux over the
-    out-of-transit samples within one transit duration of each transit, minus
-    the mean detrended flux inside transits; injected depth = mean injected
-    profile over the same in-transit samples."""
-    idx = range(batch.B) if idx is None else idx
-    errs = []
-    for b in idx:
-        s = slice(batch.offsets[b], batch.offsets[b + 1])
-        d = np.asarray(detr[s], np.float64)
-        prof = batch.transit[s].astype(np.float64)
-        n = d.size
-        cad = batch.cadence[b]
-        t = np.arange(n) * cad
-        per, ep, dur = batch.period_d[b], batch.epoch_d[b], batch.duration_d[b]
-        phase = np.abs(np.mod(t - ep + 0.5 * per, per) - 0.5 * per)
-        intr = (prof > 0) & np.isfinite(d)
-        near = (phase > 0.5 * dur) & (phase < 1.5 * dur) & np.isfinite(d)
-        if intr.sum() < 3 or near.sum() < 3:
-            continue
-        d_rec = np.median(d[near]) - np.mean(d[intr])
-        d_inj = np.mean(prof[intr])
-        errs.append(abs(d_rec - d_inj) / d_inj * 100.0)
-    return np.array(errs)
+    """Per-curve absolute percentage depth errors; the measure is the
+    package's (paper_2604_06602_gb300.injection.depth_errors)."""
+    from paper_2604_06602_gb300.injection import depth_errors
+    return depth_errors(detr, batch, idx)
