@@ -283,14 +283,13 @@ def run_umi(args):
     import torch
 
     rank, world, local = dist_env()
-    dist = init_dist(world, "nccl")
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(local)          # before NCCL init: one rank per GPU
     dev = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
     from paper_2604_06602_gb300 import build as libbuild
     from paper_2604_06602_gb300 import synth, umi
-    if rank == 0 or not libbuild.up_to_date():
-        if rank == 0:
-            libbuild.build()
+    if rank == 0:
+        libbuild.build()
     barrier(dist)
     umi.load()
 
