@@ -141,6 +141,22 @@ __device__ __forceinline__ float fma_sat(float a, float b, float c)
     return d;
 }
 
+// 1.0f when a >= b, else 0.0f (one compare, result as a float).
+__device__ __forceinline__ float ge_flag(float a, float b)
+{
+    float d;
+    asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// 1.0f when a == b, else 0.0f.
+__device__ __forceinline__ float eq_flag(float a, float b)
+{
+    float d;
+    asm("set.eq.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
 // Order-preserving map from non-NaN floats to unsigned keys (-0 sorts just
 // below +0; the counts that follow compare floats, where they are equal).
 __device__ __forceinline__ unsigned float_key(float f)
@@ -323,23 +339,30 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
 
         // ---- one-rank move of the median -----------------------------------
         if (__any_sync(0xffffffffu, move != 0)) {
+            // The two passes are built so that half their work runs on the
+            // FMA pipe, which is otherwise idle here: a 0/1 float flag marks
+            // slots at or above sm, one FFMA2 pushes them 2^127 down (slots
+            // below keep their exact value), and ties are counted as float
+            // sums of 0/1 flags (exact: at most S < 2^24).
             const float sg = (move < 0) ? -1.f : 1.f;
             const float2 sg2 = make_float2(sg, sg);
             const float sm = sg * st.m;
+            const float2 push = make_float2(-0x1p127f, -0x1p127f);
             float best = -INFINITY;
 #pragma unroll
             for (int k = 0; k < R / 2; ++k) {
                 const float2 y = __fmul2_rn(x[k], sg2);
-                best = (y.x < sm) ? fmaxf(best, y.x) : best;
-                best = (y.y < sm) ? fmaxf(best, y.y) : best;
+                const float2 f = make_float2(ge_flag(y.x, sm), ge_flag(y.y, sm));
+                const float2 yb = __ffma2_rn(f, push, y);
+                best = fmaxf(best, fmaxf(yb.x, yb.y));
             }
             best = group_max<G>(best);
             const float cand = sg * best;
-            int e = 0;
+            float2 ef = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < R / 2; ++k)
-                e += ((x[k].x == cand) ? 1 : 0) + ((x[k].y == cand) ? 1 : 0);
-            e = group_sum_int<G>(e);
+                ef = __fadd2_rn(ef, make_float2(eq_flag(x[k].x, cand), eq_flag(x[k].y, cand)));
+            const int e = group_sum_int<G>((int)(ef.x + ef.y));
             if (move > 0) {
                 st.Gp += st.E;
                 st.L -= e;
