@@ -41,8 +41,8 @@ LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of the batched kernel on this
 # workload, from one ncu capture (profiles/umi_tile_kernel_tess1000x18000.md),
 # valid only while the kernel source hashes to `kernel_sha256`.
-MEASURED_TRAFFIC = {"bytes": 164.09e6,
-                    "kernel_sha256": "46c134511af0c0b7c585f612876bbd139bb07af6f8dbebc72ca0f147d6a1e4fd"}
+MEASURED_TRAFFIC = {"bytes": 164.75e6,
+                    "kernel_sha256": "bd2437de98e1f44ffc1d0752b17173229b3ed0f3ea67099aa7b550014aabd4f1"}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2604_06602_gb300", "csrc", "umi_kernel.cuh")
 
 
@@ -309,7 +309,9 @@ def run_umi(args):
         umi.load_tuning(args.tuning_file)
     else:
         for w in sorted(set(W.tolist())):
-            umi.autotune(int(w), positions=min(int(batch.flux.size), 4_000_000))
+            # Tune at about the batch's own size (the best chain length depends on it).
+            n_w = int(batch.lengths[W == w].sum())
+            umi.autotune(int(w), positions=max(1_000_000, min(n_w, 20_000_000)))
     tuned_plan = {int(w): umi.get_plan(int(w), -1) for w in sorted(set(W.tolist()))}
     if args.save_tuning and rank == 0:
         umi.save_tuning(args.save_tuning)

@@ -174,7 +174,7 @@ __device__ __forceinline__ float key_float(unsigned k)
 // Load the window of tile position q into registers: slot s = glane + G*i
 // holds tile[q + s] for s < W, kGap past W.  Slots are stored in pairs
 // (i = 2k, 2k+1 in x[k].x, x[k].y) for the packed FP32x2 arithmetic.
-// `tail_only` (uniform) says that G*(R-1) <= W, so only the last register row
+// `tail_only` (uniform) says that G*(R-2) <= W, so only the last register pair
 // can hold slots past W; the general path re-derives each row's limit from an
 // opaque register so the compiler does not keep R loop-invariant predicates
 // alive across the chain.
@@ -189,9 +189,10 @@ __device__ __forceinline__ void load_window(float2 (&x)[R / 2], const float *til
             x[k].x = base[G * (2 * k)];
             x[k].y = base[G * (2 * k + 1)];
         }
-        x[R / 2 - 1].x = base[G * (R - 2)];
-        const float v = base[G * (R - 1)];
-        x[R / 2 - 1].y = (glane + G * (R - 1) < W) ? v : kGap;
+        const float a = base[G * (R - 2)];
+        const float b = base[G * (R - 1)];
+        x[R / 2 - 1].x = (glane + G * (R - 2) < W) ? a : kGap;
+        x[R / 2 - 1].y = (glane + G * (R - 1) < W) ? b : kGap;
     } else {
         int lim = W - glane;  // slot row i is valid for this lane iff G*i < lim
         asm volatile("" : "+r"(lim));
@@ -228,7 +229,7 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
     const float alpha = cv.alpha;
     const float cst = cv.c;
     const int iters = cv.iters;
-    const bool tail_only = G * (R - 1) <= W;  // rows 0..R-2 hold only slots < W
+    const bool tail_only = G * (R - 2) <= W;  // rows 0..R-3 hold only slots < W
     static_assert(R % 2 == 0, "slots are processed in pairs");
     float2 x[R / 2];
     MedianState st;
