@@ -128,10 +128,13 @@ umi_status umi_detrend_batched(const float *flux_d, const int64_t *offsets_h, co
 
 /*
  * umi_detrend_batched on HOST buffers: copies flux_h to the device, runs the
- * batched path and copies trend_h / detr_h back, all on `stream`, and waits
- * for the stream before returning.  Device buffers come from
- * cudaMallocAsync and are freed before return.  Pinned host memory makes the
- * copies asynchronous DMA; pageable memory works but is slower.
+ * batched path and copies trend_h / detr_h back, and waits for all of it
+ * before returning.  Batches of more than a few million samples are split
+ * into up to 8 chunks of whole curves, pipelined over `stream` and two
+ * internal copy streams so that copies overlap the detrend; the result does
+ * not depend on the chunking.  Device buffers come from cudaMallocAsync on
+ * `stream` and are freed before return.  Pinned host memory makes the copies
+ * asynchronous DMA; pageable memory works but serialises them.
  */
 umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_h,
                                     const int32_t *W_h, int32_t B, const umi_params *params,

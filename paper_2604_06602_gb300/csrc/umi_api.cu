@@ -399,6 +399,59 @@ umi_status enqueue_prepared(const std::vector<Curve> &curves, const PreparedBatc
     return enqueue_bands(pb.layout, dev, sc, stream, launches);
 }
 
+// Pinned host staging for work-queue tables: a ring of a few buffers per
+// host thread.  A copy from pageable memory would make CUDA wait for all
+// earlier work on the stream first; from pinned memory it is enqueued
+// asynchronously.  Each buffer carries an event recorded after its copy, and
+// is reused only once that event has completed (normally long since).
+namespace {
+struct PinnedSlot {
+    char *p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+};
+constexpr int kPinnedSlots = 4;
+thread_local PinnedSlot t_pinned[kPinnedSlots];  // intentionally never freed
+thread_local int t_pinned_next = 0;
+}  // namespace
+
+static umi_status acquire_pinned(size_t bytes, int *slot, char **out)
+{
+    const int k = t_pinned_next;
+    t_pinned_next = (k + 1) % kPinnedSlots;
+    PinnedSlot &ps = t_pinned[k];
+    if (ps.pending) {
+        UMI_CUDA(cudaEventSynchronize(ps.ev), "cudaEventSynchronize (staging)");
+        ps.pending = false;
+    }
+    if (!ps.ev) UMI_CUDA(cudaEventCreateWithFlags(&ps.ev, cudaEventDisableTiming), "cudaEventCreate");
+    if (ps.cap < bytes) {
+        if (ps.p) cudaFreeHost(ps.p);
+        ps.p = nullptr;
+        ps.cap = 0;
+        const size_t cap = std::max<size_t>(bytes, 64 << 10);
+        UMI_CUDA(cudaMallocHost((void **)&ps.p, cap), "cudaMallocHost (staging)");
+        ps.cap = cap;
+    }
+    *slot = k;
+    *out = ps.p;
+    return UMI_OK;
+}
+
+static void release_pinned(int slot, cudaStream_t stream)
+{
+    PinnedSlot &ps = t_pinned[slot];
+    if (cudaEventRecord(ps.ev, stream) == cudaSuccess) {
+        ps.pending = true;
+    } else {
+        // The event belongs to another device than this stream: fall back to
+        // waiting for the copy here, which keeps the buffer safe to reuse.
+        cudaGetLastError();
+        cudaStreamSynchronize(stream);
+    }
+}
+
 umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream, int *launches)
 {
     if (launches) *launches = 0;
@@ -412,15 +465,17 @@ umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t str
         if (st != UMI_OK) return st;
     }
     const Scratch sc = scratch_layout(curves.size(), lay.items.size(), lay.bands.size());
-    // Host staging in one block so a single copy moves the tables.
-    std::vector<char> host(sc.counter_off);
-    memcpy(host.data() + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
-    memcpy(host.data() + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
+    // Host staging in one pinned block so a single asynchronous copy moves the tables.
+    int slot = 0;
+    char *host = nullptr;
+    st = acquire_pinned(sc.counter_off, &slot, &host);
+    if (st != UMI_OK) return st;
+    memcpy(host + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
+    memcpy(host + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
     void *dev = nullptr;
     UMI_CUDA(cudaMallocAsync(&dev, sc.bytes, stream), "cudaMallocAsync");
-    // Pageable source: the call returns once the data are staged, so `host`
-    // may go out of scope afterwards.
-    cudaError_t e = cudaMemcpyAsync(dev, host.data(), sc.counter_off, cudaMemcpyHostToDevice, stream);
+    cudaError_t e = cudaMemcpyAsync(dev, host, sc.counter_off, cudaMemcpyHostToDevice, stream);
+    release_pinned(slot, stream);
     if (e != cudaSuccess) {
         cudaFreeAsync(dev, stream);
         return fail_cuda(e, "cudaMemcpyAsync");
@@ -822,31 +877,113 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
     clear_error();
     if (B < 0 || (B > 0 && (!offsets_h || !W_h))) return fail(UMI_ERR_INVALID_ARG, "bad batch");
     if (B == 0) return UMI_OK;
+    umi_params p;
+    umi_status st = check_params(params, &p);
+    if (st != UMI_OK) return st;
+    if (offsets_h[0] != 0) return fail(UMI_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int32_t b = 0; b < B; ++b) {
+        if (offsets_h[b + 1] < offsets_h[b]) return fail(UMI_ERR_INVALID_ARG, "offsets must be non-decreasing");
+        if (W_h[b] < 1 || (W_h[b] % 2) == 0 || W_h[b] > kMaxWindow)
+            return fail(UMI_ERR_INVALID_ARG, "W[" + std::to_string(b) + "] must be odd and in [1, " +
+                                                 std::to_string(kMaxWindow) + "]");
+    }
     const int64_t total = offsets_h[B];
-    if (total < 0) return fail(UMI_ERR_INVALID_ARG, "bad offsets");
-    if (total == 0)
-        return batched_impl(nullptr, offsets_h, W_h, B, params, nullptr, nullptr,
-                            (cudaStream_t)stream, false);
+    if (total == 0) return UMI_OK;
     if (!flux_h || !trend_h || !detr_h) return fail(UMI_ERR_INVALID_ARG, "null buffer");
+
+    // Pipeline over chunks of curves: the copy-in of chunk c+1 and the
+    // copy-out of chunk c-1 overlap the detrend of chunk c (copy engines and
+    // SMs work at once; pinned host buffers make the copies asynchronous).
+    const int64_t kChunkSamples = 2 << 20;
+    const int K = (int)std::max<int64_t>(1, std::min<int64_t>({8, B, total / kChunkSamples}));
+    std::vector<int32_t> cut(1, 0);
+    for (int c = 1; c < K; ++c) {
+        const int64_t target = total * c / K;
+        int32_t b = (int32_t)(std::upper_bound(offsets_h, offsets_h + B + 1, target) - offsets_h) - 1;
+        b = std::max(b, cut.back() + 1);
+        if (b < B) cut.push_back(b);
+    }
+    cut.push_back(B);
+
+    // Chunks alternate between the caller's stream and a second compute
+    // stream, so the next chunk's persistent kernel fills SMs while the
+    // previous one drains.
     cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_c2 = nullptr;
+    std::vector<cudaEvent_t> ev;
+    auto cleanup = [&]() {
+        if (s_in) cudaStreamDestroy(s_in);
+        if (s_out) cudaStreamDestroy(s_out);
+        if (s_c2) cudaStreamDestroy(s_c2);
+        for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    };
+    auto new_event = [&](cudaEvent_t *out) {
+        cudaError_t e = cudaEventCreateWithFlags(out, cudaEventDisableTiming);
+        if (e == cudaSuccess) ev.push_back(*out);
+        return e;
+    };
     const size_t bytes = sizeof(float) * (size_t)total;
     float *dev = nullptr;
-    UMI_CUDA(cudaMallocAsync((void **)&dev, 3 * bytes, s), "cudaMallocAsync");
-    umi_status st = UMI_OK;
-    cudaError_t e = cudaMemcpyAsync(dev, flux_h, bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) st = fail_cuda(e, "cudaMemcpyAsync H2D");
-    if (st == UMI_OK) {
-        // The graph cache is keyed by device pointers, which change per call here.
-        st = batched_impl(dev, offsets_h, W_h, B, params, dev + total, dev + 2 * total, s, false);
+    cudaError_t e = cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_c2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dev, 3 * bytes, s);
+    cudaEvent_t ev_alloc = nullptr;
+    if (e == cudaSuccess) e = new_event(&ev_alloc);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_alloc, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev_alloc, 0);
+    if (e != cudaSuccess) {
+        if (dev) cudaFreeAsync(dev, s);
+        cudaStreamSynchronize(s);
+        cleanup();
+        return fail_cuda(e, "batched host pipeline setup");
     }
-    if (st == UMI_OK) {
-        e = cudaMemcpyAsync(trend_h, dev + total, bytes, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(detr_h, dev + 2 * total, bytes, cudaMemcpyDeviceToHost, s);
+    float *dflux = dev, *dtrend = dev + total, *ddetr = dev + 2 * total;
+    std::vector<int64_t> off_c;
+    for (size_t c = 0; c + 1 < cut.size() && st == UMI_OK; ++c) {
+        const int32_t b0 = cut[c], b1 = cut[c + 1];
+        const int64_t o = offsets_h[b0], n = offsets_h[b1] - o;
+        cudaEvent_t ev_in = nullptr, ev_done = nullptr;
+        e = new_event(&ev_in);
+        if (e == cudaSuccess) e = new_event(&ev_done);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpyAsync(dflux + o, flux_h + o, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, s_in);
+        cudaStream_t cs = (c % 2 == 0) ? s : s_c2;
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in, s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in, 0);
+        if (e != cudaSuccess) {
+            st = fail_cuda(e, "cudaMemcpyAsync H2D");
+            break;
+        }
+        off_c.assign(offsets_h + b0, offsets_h + b1 + 1);
+        for (auto &x : off_c) x -= o;
+        st = batched_impl(dflux + o, off_c.data(), W_h + b0, b1 - b0, &p, dtrend + o, ddetr + o, cs, false);
+        if (st != UMI_OK) break;
+        e = cudaEventRecord(ev_done, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_done, 0);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpyAsync(trend_h + o, dtrend + o, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s_out);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpyAsync(detr_h + o, ddetr + o, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s_out);
         if (e != cudaSuccess) st = fail_cuda(e, "cudaMemcpyAsync D2H");
     }
+    // The caller's stream waits for every copy and the second compute
+    // stream, then frees the buffers.
+    cudaEvent_t ev_out = nullptr, ev_c2 = nullptr;
+    if (new_event(&ev_out) == cudaSuccess && new_event(&ev_c2) == cudaSuccess) {
+        cudaEventRecord(ev_out, s_out);
+        cudaEventRecord(ev_c2, s_c2);
+        cudaStreamWaitEvent(s, ev_out, 0);
+        cudaStreamWaitEvent(s, ev_c2, 0);
+    } else {
+        cudaStreamSynchronize(s_out);
+        cudaStreamSynchronize(s_c2);
+    }
+    cudaStreamSynchronize(s_in);
     cudaFreeAsync(dev, s);
     e = cudaStreamSynchronize(s);
     if (st == UMI_OK && e != cudaSuccess) st = fail_cuda(e, "cudaStreamSynchronize");
+    cleanup();
     return st;
 }
 

@@ -341,3 +341,23 @@ def test_mad_degenerate_and_ties(umi):
     got = run_diag(umi, x, 61, p)
     ref = oracle.detrend(x, 61, scale_mode=oracle.SCALE_MAD)
     compare_diag(got, ref, what="MAD ties")
+
+
+def test_host_entry_point_pipelined_chunks_identical(umi):
+    """Large host batches are split into pipelined chunks of whole curves;
+    the output must equal the device-resident batched call bit for bit."""
+    b = synth.config3(n_curves=400)                 # about 1e7 samples, mixed windows
+    W = np.array([umi.window_length(c) for c in b.cadence], np.int32)
+    umi.set_graph_cache(False)
+    t0, d0 = umi.detrend_batched(torch.from_numpy(b.flux).cuda(), b.offsets, W)
+    umi.set_graph_cache(True)
+    fh = torch.from_numpy(b.flux).pin_memory()
+    th = torch.empty(b.flux.size, dtype=torch.float32).pin_memory()
+    dh = torch.empty(b.flux.size, dtype=torch.float32).pin_memory()
+    umi.detrend_batched_host(fh, b.offsets, W, trend=th, detr=dh)
+    assert b.flux.size > 4 * (2 << 20)
+    assert np.array_equal(th.numpy(), t0.cpu().numpy(), equal_nan=True)
+    assert np.array_equal(dh.numpy(), d0.cpu().numpy(), equal_nan=True)
+    # Pageable numpy buffers take the same path (copies serialise).
+    tn, dn = umi.detrend_batched_host(b.flux, b.offsets, W)
+    assert np.array_equal(tn, t0.cpu().numpy(), equal_nan=True)
