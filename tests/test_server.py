@@ -169,3 +169,25 @@ def test_wait_timeout_is_reported(umi):
         srv.release(a)
         srv.wait(b, 60.0)
         srv.release(b)
+
+
+def test_mixed_scale_modes_and_params_in_one_batch(umi):
+    """Requests with different parameters (including the MAD scale, which
+    runs a different kernel build) share batches and still match their own
+    single-curve results."""
+    mix = curves_mix(18)
+    presets = [umi.params(), umi.params(alpha=1.0, scale_mode=umi.SCALE_MAD),
+               umi.params(alpha=10.0, c=2.5), umi.params(iters=2, min_valid=0)]
+    with umi.Server(mem_budget_bytes=1 << 30, n_streams=1, max_batch_curves=64,
+                    max_wait_s=0.5) as srv:
+        tickets = [srv.submit(x, W, presets[i % len(presets)]) for i, (x, W) in enumerate(mix)]
+        for t in tickets:
+            srv.wait(t, 120.0)
+        assert srv.stats()["batches_launched"] <= 3
+        for i, ((x, W), t) in enumerate(zip(mix, tickets)):
+            tr, _ = srv.copy_out(t, x.size)
+            xd = torch.from_numpy(x).cuda()
+            ta, _ = umi.detrend(xd, W, presets[i % len(presets)])
+            torch.cuda.synchronize()
+            assert np.array_equal(tr, ta.cpu().numpy(), equal_nan=True)
+            srv.release(t)
