@@ -94,3 +94,21 @@ def test_version(lib):
 
 def test_built_for_sm103a_only():
     assert libbuild.ARCH_FLAGS == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_header_is_c99_and_host_calls_work(tmp_path, lib):
+    """Compile a C99 program against include/umi.h, link libumi.so and run
+    its host-only calls (no GPU needed)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    exe = tmp_path / "c_abi_check"
+    libdir = os.path.dirname(umi.lib_path())
+    src = os.path.join(ROOT, "tests", "c_abi_check.c")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    src, "-o", str(exe), "-L", libdir, "-lumi", "-Wl,-rpath," + libdir],
+                   check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert "sm_103a" in r.stdout
