@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/umi.h"
+#include "umi.h"
 #include "umi_kernel.cuh"
 #include "umi_variants.h"
 

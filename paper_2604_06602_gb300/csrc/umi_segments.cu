@@ -44,7 +44,6 @@ namespace {
 // Reader over the 32-bit-word validity mask: word-at-a-time run scans.
 struct Bits {
     const unsigned *w;
-    bool get(int64_t i) const { return (w[i >> 5] >> (i & 31)) & 1u; }
     // First index in [i, end) whose bit equals `want`, or end.
     int64_t find(int64_t i, int64_t end, bool want) const
     {
