@@ -504,6 +504,30 @@ def serve_at_rate(umi, srv, dev_pool, Ws, which, arrivals, n):
     return np.array(lat), time.perf_counter() - t0, n / t_sub
 
 
+def serialized_at_rate(umi, torch, dev_pool, Ws, which, arrivals, n, trend, detr):
+    """The same request stream served by one umi_detrend launch per request
+    on one stream (the plain form).  Latency runs from the launch call to the
+    completion of its event."""
+    stream = torch.cuda.Stream()
+    lat, pend = [], []
+    t0 = time.perf_counter()
+    i = 0
+    while i < n or pend:
+        now = time.perf_counter()
+        if i < n and now >= t0 + arrivals[i]:
+            k = int(which[i])
+            t_sub = time.perf_counter()
+            umi.detrend(dev_pool[k], Ws[k], trend=trend[k], detr=detr[k], stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            pend.append((ev, t_sub))
+            i += 1
+            continue
+        if pend and pend[0][0].query():
+            lat.append(time.perf_counter() - pend.pop(0)[1])
+    return np.array(lat), time.perf_counter() - t0
+
+
 def serving_leg(umi, torch, dev, args):
     """Poisson arrivals of mixed-size curves into the continuous-batching
     server (inputs resident on the device) at several offered rates, against
@@ -546,6 +570,13 @@ def serving_leg(umi, torch, dev, args):
         umi.detrend(dev_pool[k], Ws[k], trend=trend[k], detr=detr[k])
     torch.cuda.synchronize()
     out["serialized_per_curve_curves_per_s"] = nser / (time.perf_counter() - s0)
+    out["serialized_rates"] = []
+    for rate in (1000.0, 5000.0, 20000.0):
+        n = int(min(n_max, max(1000, rate * 0.3)))
+        lat, wall = serialized_at_rate(umi, torch, dev_pool, Ws, which, arrivals / rate, n, trend, detr)
+        out["serialized_rates"].append({"rate_hz": rate, "requests": n, "curves_per_s": n / wall,
+                                        "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                                        "p99_ms": float(np.percentile(lat, 99) * 1e3)})
     best = max(out["rates"], key=lambda r: r["curves_per_s"])
     out["p50_ms"], out["p99_ms"] = best["p50_ms"], best["p99_ms"]
     out["curves_per_s"] = best["curves_per_s"]

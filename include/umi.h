@@ -274,6 +274,11 @@ typedef struct {
     int32_t device;            /* CUDA device ordinal (default 0) */
     double max_wait_s;         /* longest a request waits to be batched while a
                                   stream is idle (default 0: launch at once) */
+    int32_t busy_poll;         /* 1 (default): the scheduler thread spins, polling
+                                  for new requests and for finished batches with
+                                  cudaEventQuery (lowest latency, one host core
+                                  busy); 0: it sleeps on a condition variable and
+                                  learns of finished batches from host callbacks */
 } umi_server_config;
 
 typedef struct {

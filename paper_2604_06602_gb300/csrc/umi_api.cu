@@ -284,11 +284,17 @@ umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout)
     variant_table(&nvar);
     // One band per distinct plan (variant, chain, threads), in descending
     // slot capacity so that the heaviest tiles start first.
+    // Positions per (window length, flavour): a small band gets shorter chains
+    // so that its work still spreads over the whole GPU (make_plan).
+    std::map<std::pair<int, int>, int64_t> band_positions;
+    for (const Curve &c : curves)
+        band_positions[std::make_pair(c.W, c.scale_mode)] += c.n;
     std::map<std::tuple<int, int, int, int, int>, std::vector<int>> by_plan;
     std::vector<Plan> plans;
     for (size_t b = 0; b < curves.size(); ++b) {
         Plan p;
-        umi_status st = make_plan(curves[b].W, -1, &p);
+        umi_status st =
+            make_plan(curves[b].W, band_positions[std::make_pair(curves[b].W, curves[b].scale_mode)], &p);
         if (st != UMI_OK) return st;
         const int flavour = curves[b].scale_mode == UMI_SCALE_MAD ? kFlagMad : 0;
         by_plan[std::make_tuple(-p.G * p.R, p.variant, p.chain, p.threads, flavour)].push_back((int)b);

@@ -11,9 +11,10 @@
 //      max_batch_curves), enqueues their host-input copies (device inputs are
 //      read in place) and one batched launch
 //      (the persistent work-queue kernel of umi_api.cu) on that stream, then a
-//      host callback that timestamps completion, so up to n_streams batches
-//      run on the GPU at once while new requests keep arriving;
-//   3. marks requests done when their batch's callback fires.
+//      completion marker (an event the scheduler polls, or a host callback),
+//      so up to n_streams batches run on the GPU at once while new requests
+//      keep arriving;
+//   3. marks requests done when their batch's marker has fired.
 // Results stay in the arena until umi_server_release.  A batch that fails to
 // launch fails only its own requests; the server keeps serving.
 #include <cuda_runtime.h>
@@ -126,6 +127,7 @@ struct umi_server {
     char *arena = nullptr;
     std::unique_ptr<ArenaAllocator> alloc;
     std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done_events;  // busy-poll mode: one per stream
     std::vector<StreamBuffers> bufs;  // one per stream; a stream runs one batch at a time
     std::vector<std::shared_ptr<Batch>> inflight;  // one slot per stream
     std::mutex mu;
@@ -142,6 +144,7 @@ struct umi_server {
     double batch_curves_sum = 0;
     int inject_launch_failures = 0;
     int inject_alloc_failures = 0;
+    std::atomic<uint64_t> change_seq{0};  // bumped by submit / release (busy-poll wake-up)
 };
 
 namespace umi {
@@ -219,7 +222,17 @@ static void reap_locked(umi_server *s)
 {
     for (size_t k = 0; k < s->inflight.size(); ++k) {
         auto &b = s->inflight[k];
-        if (!b || !b->done.load()) continue;
+        if (!b) continue;
+        if (s->cfg.busy_poll && !b->done.load()) {
+            const cudaError_t q = cudaEventQuery(s->done_events[k]);
+            if (q == cudaSuccess) {
+                b->t_done = now_s();
+                b->done.store(true);
+            } else if (q != cudaErrorNotReady) {
+                cudaGetLastError();
+            }
+        }
+        if (!b->done.load()) continue;
         for (uint64_t t : b->tickets) {
             auto it = s->reqs.find(t);
             if (it == s->reqs.end()) continue;
@@ -323,7 +336,11 @@ static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mute
         else ok = false;
     }
     if (ok && enqueue_prepared(curves, pb, sb.dev, sb.host, st, &launches) != UMI_OK) ok = false;
-    if (ok && cudaLaunchHostFunc(st, batch_done_cb, batch.get()) != cudaSuccess) ok = false;
+    if (ok) {
+        const cudaError_t e = s->cfg.busy_poll ? cudaEventRecord(s->done_events[k], st)
+                                               : cudaLaunchHostFunc(st, batch_done_cb, batch.get());
+        if (e != cudaSuccess) ok = false;
+    }
     const double t_enq = now_s() - t_enq0;
 
     lk.lock();
@@ -350,24 +367,50 @@ static void scheduler_main(umi_server *s)
     while (!s->stop) {
         reap_locked(s);
         admit_locked(s);
+        bool hold = false;
         if (s->cfg.max_wait_s > 0.0 && !s->admitted.empty() && s->pending.empty() &&
             s->admitted.size() < (size_t)s->cfg.max_batch_curves) {
             // Hold a small batch back a little so that it can grow.
             const double age = now_s() - s->reqs[s->admitted.front()]->t_submit;
             if (age < s->cfg.max_wait_s) {
-                s->cv_sched.wait_for(lk, std::chrono::duration<double>(s->cfg.max_wait_s - age));
-                continue;
+                if (!s->cfg.busy_poll) {
+                    s->cv_sched.wait_for(lk, std::chrono::duration<double>(s->cfg.max_wait_s - age));
+                    continue;
+                }
+                hold = true;
             }
         }
         bool launched = false;
-        for (size_t k = 0; k < s->streams.size() && !s->admitted.empty(); ++k) {
+        for (size_t k = 0; !hold && k < s->streams.size() && !s->admitted.empty(); ++k) {
             if (s->inflight[k]) continue;
             launch_batch_locked(s, (int)k, lk);
             launched = true;
             if (s->stop) break;
         }
         if (launched) continue;
-        s->cv_sched.wait_for(lk, std::chrono::microseconds(500));
+        if (s->cfg.busy_poll) {
+            // Spin without the lock until a request arrives or is released, a
+            // batch in flight finishes, or 200 us pass.  Only this thread
+            // touches `inflight` and the events, so they are read unlocked.
+            const uint64_t seen = s->change_seq.load();
+            std::vector<int> busy;
+            for (size_t k = 0; k < s->inflight.size(); ++k)
+                if (s->inflight[k]) busy.push_back((int)k);
+            const bool holding = hold;
+            lk.unlock();
+            const double t_spin = now_s();
+            for (;;) {
+                if (s->stop || s->change_seq.load() != seen) break;
+                bool finished = false;
+                for (int k : busy)
+                    if (cudaEventQuery(s->done_events[k]) != cudaErrorNotReady) finished = true;
+                if (finished || holding || now_s() - t_spin > 200e-6) break;
+                std::this_thread::yield();
+            }
+            lk.lock();
+        } else {
+            s->cv_sched.wait_for(lk, std::chrono::microseconds(500));
+        }
     }
 }
 
@@ -384,6 +427,7 @@ void umi_server_default_config(umi_server_config *cfg)
     cfg->max_batch_curves = 1024;
     cfg->device = 0;
     cfg->max_wait_s = 0.0;
+    cfg->busy_poll = 1;
 }
 
 umi_status umi_server_create(const umi_server_config *cfg_in, umi_server **out)
@@ -405,13 +449,17 @@ umi_status umi_server_create(const umi_server_config *cfg_in, umi_server **out)
     if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc (server arena)");
     s->alloc.reset(new ArenaAllocator(cfg.mem_budget_bytes));
     s->streams.resize(cfg.n_streams);
+    s->done_events.resize(cfg.n_streams);
     s->bufs.resize(cfg.n_streams);
     s->inflight.resize(cfg.n_streams);
-    for (auto &st : s->streams) {
-        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (int k = 0; k < cfg.n_streams; ++k) {
+        e = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->done_events[k], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             for (auto &x : s->streams)
                 if (x) cudaStreamDestroy(x);
+            for (auto &x : s->done_events)
+                if (x) cudaEventDestroy(x);
             cudaFree(s->arena);
             return fail_cuda(e, "cudaStreamCreate");
         }
@@ -459,6 +507,7 @@ umi_status umi_server_submit(umi_server *s, const float *flux, int is_device_ptr
         s->stats.submitted++;
         s->stats.queued_requests = s->pending.size();
     }
+    s->change_seq.fetch_add(1);
     s->cv_sched.notify_one();
     return UMI_OK;
 }
@@ -552,6 +601,7 @@ umi_status umi_server_release(umi_server *s, uint64_t ticket)
         s->reqs.erase(it);
         s->stats.released++;
     }
+    s->change_seq.fetch_add(1);
     s->cv_sched.notify_one();
     return UMI_OK;
 }
@@ -595,6 +645,7 @@ void umi_server_destroy(umi_server *s)
         if (b.dev) cudaFree(b.dev);
         if (b.host) cudaFreeHost(b.host);
     }
+    for (auto &x : s->done_events) cudaEventDestroy(x);
     s->inflight.clear();
     if (s->arena) cudaFree(s->arena);
     delete s;

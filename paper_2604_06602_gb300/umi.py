@@ -75,7 +75,8 @@ class SegmentParams(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("max_batch_curves", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("max_wait_s", ctypes.c_double)]
+                ("device", ctypes.c_int32), ("max_wait_s", ctypes.c_double),
+                ("busy_poll", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -371,7 +372,7 @@ class Server:
     """Continuous-batching server (umi_server_*)."""
 
     def __init__(self, mem_budget_bytes=None, max_slots=None, n_streams=None, max_batch_curves=None,
-                 device=0, max_wait_s=None):
+                 device=0, max_wait_s=None, busy_poll=None):
         cfg = ServerConfig()
         load().umi_server_default_config(ctypes.byref(cfg))
         if mem_budget_bytes is not None:
@@ -384,6 +385,8 @@ class Server:
             cfg.max_batch_curves = int(max_batch_curves)
         if max_wait_s is not None:
             cfg.max_wait_s = float(max_wait_s)
+        if busy_poll is not None:
+            cfg.busy_poll = int(busy_poll)
         cfg.device = int(device)
         h = ctypes.c_void_p()
         _check(load().umi_server_create(ctypes.byref(cfg), ctypes.byref(h)))

@@ -45,9 +45,11 @@ def alone(umi, x, W):
     return t.cpu().numpy(), d.cpu().numpy()
 
 
-def test_alone_equals_mix(umi):
+@pytest.mark.parametrize("busy_poll", [1, 0])
+def test_alone_equals_mix(umi, busy_poll):
     mix = curves_mix()
-    with umi.Server(mem_budget_bytes=1 << 30, n_streams=3, max_batch_curves=8) as srv:
+    with umi.Server(mem_budget_bytes=1 << 30, n_streams=3, max_batch_curves=8,
+                    busy_poll=busy_poll) as srv:
         tickets = [srv.submit(x, W) for x, W in mix]
         for t in tickets:
             srv.wait(t, 120.0)
@@ -122,12 +124,13 @@ def test_errors(umi):
         assert srv.stats()["rejected"] == 1
 
 
-def test_injected_failures_only_hit_their_requests(umi):
+@pytest.mark.parametrize("busy_poll", [1, 0])
+def test_injected_failures_only_hit_their_requests(umi, busy_poll):
     mix = curves_mix(12)
     # max_wait_s holds a partial batch back, so the four requests submitted
     # together form one batch of max_batch_curves = 4.
     with umi.Server(mem_budget_bytes=1 << 30, n_streams=1, max_batch_curves=4,
-                    max_wait_s=2.0) as srv:
+                    max_wait_s=2.0, busy_poll=busy_poll) as srv:
         srv.inject_fault(1, 1)                        # the next batch fails to launch
         first = [srv.submit(x, W) for x, W in mix[:4]]
         for t in first:
