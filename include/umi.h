@@ -38,6 +38,9 @@
  *     Errors are returned, never raised by abort().  umi_last_error() gives a
  *     message for the calling thread's most recent failure.
  *   - Calls are thread-safe.  Calls on different streams may overlap.
+ *   - Do not capture calls of this library into your own CUDA graph: the
+ *     batched paths keep their own graph cache and stage their work tables
+ *     through reused host buffers, which a captured copy would not see again.
  */
 #ifndef UMI_H
 #define UMI_H

@@ -80,8 +80,9 @@ static const int kMaxWindow = 4095;
 
 bool legal_chain(int G, int chain)
 {
-    // Groups of one warp start G*chain/G... apart in the tile; a chain of
-    // G * odd positions puts the 32/G groups of a warp on disjoint banks.
+    // The 32/G groups of a warp start `chain` positions apart in the tile, so
+    // their G-lane loads hit banks (g * chain + lane) mod 32; a chain of
+    // G * (odd number) positions keeps the groups on disjoint banks.
     if (chain < 1) return false;
     if (G >= 32) return true;
     return chain % G == 0 && ((chain / G) & 1) == 1;

@@ -204,12 +204,6 @@ def _dev_f32(t, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _ptr_or_null(t, dtype_name):
-    if t is None:
-        return None
-    return ctypes.c_void_p(t.data_ptr())
-
-
 def detrend(flux, W, p: Params | None = None, trend=None, detr=None, stream=None):
     """One curve on the GPU.  Returns (trend, detr) float32 CUDA tensors."""
     import torch
