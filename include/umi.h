@@ -38,9 +38,10 @@
  *     Errors are returned, never raised by abort().  umi_last_error() gives a
  *     message for the calling thread's most recent failure.
  *   - Calls are thread-safe.  Calls on different streams may overlap.
- *   - Do not capture calls of this library into your own CUDA graph: the
- *     batched paths keep their own graph cache and stage their work tables
- *     through reused host buffers, which a captured copy would not see again.
+ *   - umi_detrend_batched, umi_detrend_batched_host and umi_detrend_segmented
+ *     keep their own CUDA-graph cache and stage their work tables through
+ *     reused pinned host buffers; do not capture them into a graph of your
+ *     own (a captured table copy would not see the buffer's later contents).
  */
 #ifndef UMI_H
 #define UMI_H
