@@ -309,9 +309,13 @@ def run_umi(args):
         umi.load_tuning(args.tuning_file)
     else:
         for w in sorted(set(W.tolist())):
-            # Tune at about the batch's own size (the best chain length depends on it).
+            # Tune at about the batch's own size (the best chain length depends on it),
+            # and, where one curve alone is a latency-regime band, at a median curve.
             n_w = int(batch.lengths[W == w].sum())
             umi.autotune(int(w), positions=max(1_000_000, min(n_w, 20_000_000)))
+            n_one = int(np.median(batch.lengths[W == w]))
+            if n_one > 0 and umi.get_plan(int(w), n_one)["latency"]:
+                umi.autotune(int(w), positions=n_one)
     tuned_plan = {int(w): umi.get_plan(int(w), -1) for w in sorted(set(W.tolist()))}
     if args.save_tuning and rank == 0:
         umi.save_tuning(args.save_tuning)
@@ -540,7 +544,11 @@ def serving_leg(umi, torch, dev, args):
     dev_pool = [torch.from_numpy(x).to(dev) for x in pool]
     sizes = np.array([x.size for x in pool])
     for w in sorted(set(Ws)):
+        # Both regimes: large batches, and a median request of this window length.
         umi.autotune(w, positions=2_000_000)
+        n_one = int(np.median([pool[k].size for k in range(len(pool)) if Ws[k] == w]))
+        if umi.get_plan(w, n_one)["latency"]:
+            umi.autotune(w, positions=n_one)
     torch.cuda.synchronize()
     out = {"mixture": "45% TESS 2-min N 5k-20k W=361, 45% Kepler N 4k-70k W=25, "
                       "10% 20-s N 60k-118k W=2161", "mean_samples": float(sizes[which].mean()),

@@ -226,10 +226,21 @@ umi_status umi_detrend_segmented(const float *flux_d, const int64_t *offsets_h, 
 int32_t umi_max_window(void);
 
 /*
- * Kernel plan chosen for a window length and a problem size (positions to
- * evaluate), for inspection and tuning.  `lanes` = lanes per window (1-32),
- * `slots` = register slots per lane, `chain` = consecutive positions per lane
- * group, `threads` = threads per CTA.
+ * Kernel plan chosen for a window length and a band size (`positions` =
+ * windows of that length in one launch; <= 0 means a band large enough for
+ * the longest chain), for inspection and tuning.  `lanes` = lanes per window
+ * (1-32), `slots` = register slots per lane, `chain` = consecutive positions
+ * per lane group, `threads` = threads per CTA, `latency` = 1 when the band is
+ * too small to fill the GPU at the shortest chain of the throughput variant
+ * (then a 32-lane variant is used where one covers W within 2W, so that
+ * every window can start its own chain).
+ *
+ * Every call plans each band from its own size, so the same curve can run on
+ * different variants alone and inside a large batch.  Variants differ only in
+ * how the FP32 sums of Eqs. 1 and 4 are split over lanes: the median and the
+ * above-median set are the same, and the trends differ only by the rounding
+ * of those sums (well inside 1e-5 relative).  Calls whose bands plan to the
+ * same variant give bit-identical results.
  */
 typedef struct {
     int32_t lanes;
@@ -237,6 +248,7 @@ typedef struct {
     int32_t chain;
     int32_t threads;
     int32_t variant; /* index into the compiled variant table */
+    int32_t latency; /* 1: latency regime, 0: throughput regime */
 } umi_plan;
 
 umi_status umi_get_plan(int32_t W, int64_t positions, umi_plan *plan);
@@ -244,10 +256,18 @@ umi_status umi_get_plan(int32_t W, int64_t positions, umi_plan *plan);
 /*
  * Autotuner.  Times every eligible (lanes, slots, chain, threads) choice for
  * window length W on a synthetic flux-like curve of `positions` samples on
- * `stream` (blocking), and records the fastest for W's band.  Later calls
- * use the recorded plan.  umi_save_tuning / umi_load_tuning persist the
- * table as text lines "gpu|W|G|R|MINB|chain|threads" keyed by GPU name
- * (MINB: the register budget of the variant, in CTAs of 256 threads per SM).
+ * `stream` (blocking), and records the fastest for W in the regime of that
+ * band size (see umi_plan: latency or throughput); later bands of W in the
+ * same regime use it (a band smaller than `positions` gets the planner's own
+ * chain for its size times the ratio the tuner preferred at `positions`, if
+ * that is shorter).  umi_save_tuning / umi_load_tuning persist the table
+ * as text lines "gpu|W|regime|G|R|MINB|chain|threads|positions" (regime
+ * "latency" or "throughput"; a line without the regime field is a throughput
+ * plan; without `positions`, smaller bands get the planner's own chain when
+ * it is shorter) keyed by GPU name (MINB: the register budget of the
+ * variant, in CTAs of 256 threads per SM).
+ * Lines for other GPUs are skipped; a malformed line fails the load and
+ * leaves the table unchanged.
  */
 umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *best,
                         double *best_ms);

@@ -88,41 +88,140 @@ bool legal_chain(int G, int chain)
     return chain % G == 0 && ((chain / G) & 1) == 1;
 }
 
-static int round_chain(int G, int target)
+// Smallest legal chain of at least `target` positions.
+static int chain_at_least(int G, int64_t target)
 {
-    if (G >= 32) return std::max(1, target);
-    int odd = std::max(1, target / G);
-    if ((odd & 1) == 0) odd += 1;
-    return G * odd;
+    target = std::min<int64_t>(std::max<int64_t>(target, 1), 1 << 20);
+    if (G >= 32) return (int)target;
+    int64_t odd = (target + G - 1) / G;
+    if ((odd & 1) == 0) ++odd;
+    return (int)(G * odd);
 }
 
+static int shortest_chain(int G) { return G >= 32 ? 1 : G; }
+// Longest chain the planner uses: about 136 positions for groups of 8 or more
+// lanes, about 33 for narrower groups (whose tile is already 32 windows wide).
+static int chain_cap(int G) { return chain_at_least(G, G >= 8 ? 136 : 33); }
 static int default_threads(int G) { return G <= 2 ? 128 : 256; }
-static int default_chain(int G)
-{
-    switch (G) {
-    case 1: return 33;
-    case 2: return 34;
-    case 4: return 36;
-    case 8: return 136;
-    case 16: return 80;
-    default: return 64;
-    }
-}
 
-// Tuned plans, keyed by window length (filled by umi_autotune / umi_load_tuning).
-// Every change bumps g_tune_epoch, which is part of the CUDA-graph cache key,
-// so a cached graph never replays a plan that is no longer current.
+// Planning constants, measured on GB300 over window lengths 25 to 2161 and
+// bands of 1e4 to 3e6 positions:
+//  * the chain is sized so that about kWarpsPerSm warps per SM get a tile;
+//  * a band is in the latency regime when, even at the shortest chain of its
+//    throughput variant, it has fewer than kLatencyItemsPerSm tiles per SM;
+//  * below kRegisterRichBelow positions the variant with the larger register
+//    budget wins (the tighter budget pays only once many warps share an SM);
+//  * below kSmallCtaBelow positions 128-thread CTAs spread a band more evenly.
+static const int kWarpsPerSm = 16;
+static const int kLatencyItemsPerSm = 32;
+static const int64_t kRegisterRichBelow = 3000000;
+static const int64_t kSmallCtaBelow = 300000;
+
+// Tuned plans, keyed by (window length, regime) (filled by umi_autotune /
+// umi_load_tuning).  Every change bumps g_tune_epoch, which is part of the
+// CUDA-graph cache key, so a cached graph never replays a plan that is no
+// longer current.
 static std::mutex g_tune_mu;
-static std::map<int, Plan> g_tuned;
+static std::map<std::pair<int, int>, Plan> g_tuned;
 static std::atomic<uint64_t> g_tune_epoch{0};
 
-static int pick_variant(int W)
+static int smallest_capacity(int W)
 {
     int n = 0;
     const Variant *t = variant_table(&n);
+    int best = 1 << 30;
     for (int v = 0; v < n; ++v)
-        if (t[v].G * t[v].R >= W) return v;
-    return -1;
+        if (t[v].G * t[v].R >= W) best = std::min(best, t[v].G * t[v].R);
+    return best;
+}
+
+// Capacity S covers W and wastes at most a third of it (the smallest covering
+// capacity always qualifies).
+static bool tight_fit(const Variant &v, int W, int smallest)
+{
+    const int S = v.G * v.R;
+    return S >= W && (S == smallest || 3 * S <= 4 * W);
+}
+
+// Variant for bands that fill the GPU: the smallest covering capacity; below
+// kRegisterRichBelow positions, the tight fit with the largest register budget
+// (lowest MINB), then the smallest capacity.
+static int throughput_variant(int W, int64_t positions)
+{
+    int n = 0;
+    const Variant *t = variant_table(&n);
+    const int smallest = smallest_capacity(W);
+    const bool rich = positions > 0 && positions < kRegisterRichBelow;
+    int best = -1;
+    for (int v = 0; v < n; ++v) {
+        if (!tight_fit(t[v], W, smallest)) continue;
+        if (best < 0) {
+            best = v;
+            continue;
+        }
+        const Variant &a = t[v], &b = t[best];
+        const int Sa = a.G * a.R, Sb = b.G * b.R;
+        if (rich ? (a.minb < b.minb || (a.minb == b.minb && Sa < Sb)) : Sa < Sb) best = v;
+    }
+    return best;
+}
+
+// Variant for bands too small to fill the GPU.  A group narrower than a warp
+// needs a chain of at least G positions, so its tile is at least 32 windows
+// and the band yields at most positions/32 tiles; a 32-lane group can run a
+// chain of 1.  So when a 32-lane variant covers W within 2W (or is the
+// smallest covering capacity), it is used -- a tight fit first, then the
+// largest register budget, then the smallest capacity; otherwise the
+// throughput variant stays.
+static int latency_variant(int W, int64_t positions)
+{
+    int n = 0;
+    const Variant *t = variant_table(&n);
+    const int smallest = smallest_capacity(W);
+    int best = -1;
+    for (int v = 0; v < n; ++v) {
+        const int S = t[v].G * t[v].R;
+        if (t[v].G != 32 || S < W || (S != smallest && S > 2 * W)) continue;
+        if (best < 0) {
+            best = v;
+            continue;
+        }
+        const Variant &a = t[v], &b = t[best];
+        const bool ta = tight_fit(a, W, smallest), tb = tight_fit(b, W, smallest);
+        if (ta != tb) {
+            if (ta) best = v;
+            continue;
+        }
+        if (a.minb != b.minb) {
+            if (a.minb < b.minb) best = v;
+            continue;
+        }
+        if (S < b.G * b.R) best = v;
+    }
+    return best >= 0 ? best : throughput_variant(W, positions);
+}
+
+int plan_regime(int W, int64_t positions)
+{
+    if (positions <= 0) return kRegimeThroughput;
+    const int v = throughput_variant(W, positions);
+    if (v < 0) return kRegimeThroughput;
+    int n = 0;
+    const Variant *t = variant_table(&n);
+    const int G = t[v].G;
+    const int64_t tile = (int64_t)(32 / G) * shortest_chain(G);
+    const int64_t items = (positions + tile - 1) / tile;
+    const int sms = std::max(1, device_info(current_device()).sms);
+    return items < (int64_t)kLatencyItemsPerSm * sms ? kRegimeLatency : kRegimeThroughput;
+}
+
+// Chain for `positions` windows: about kWarpsPerSm warps per SM get a tile.
+static int chain_for(int G, int64_t positions)
+{
+    const int sms = std::max(1, device_info(current_device()).sms);
+    const int64_t warps = (int64_t)sms * kWarpsPerSm;
+    const int64_t per_warp = (positions + warps - 1) / warps;  // windows per warp tile
+    return chain_at_least(G, (per_warp * G + 31) / 32);       // 32/G groups share a tile
 }
 
 umi_status make_plan(int W, int64_t positions, Plan *plan)
@@ -131,38 +230,40 @@ umi_status make_plan(int W, int64_t positions, Plan *plan)
         return fail(UMI_ERR_INVALID_ARG, "W must be odd and in [1, " + std::to_string(kMaxWindow) + "]");
     int n = 0;
     const Variant *t = variant_table(&n);
+    const int regime = plan_regime(W, positions);
+    Plan p;
+    bool tuned = false;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tuned.find(W);
+        auto it = g_tuned.find(std::make_pair(W, regime));
         if (it != g_tuned.end()) {
-            Plan p = it->second;
-            // A tuned plan sized for large batches is kept for small work too,
-            // except that the chain shrinks so the GPU still fills up.
-            if (positions > 0) {
-                const int sms = device_info(current_device()).sms;
-                const int64_t groups = std::max<int64_t>(1, (int64_t)sms * 4 * (p.threads / p.G));
-                const int64_t want = (positions + groups - 1) / groups;
-                if (want < p.chain) p.chain = round_chain(p.G, (int)want);
-            }
-            *plan = p;
-            return UMI_OK;
+            p = it->second;
+            tuned = true;
         }
     }
-    const int v = pick_variant(W);
-    if (v < 0) return fail(UMI_ERR_INVALID_ARG, "no kernel variant for W=" + std::to_string(W));
-    Plan p;
-    p.variant = v;
-    p.G = t[v].G;
-    p.R = t[v].R;
-    p.threads = default_threads(p.G);
-    p.chain = default_chain(p.G);
-    if (positions > 0) {
-        // Small problems: shorten the chain so that about 4 CTAs per SM exist.
-        const int sms = std::max(1, device_info(current_device()).sms);
-        const int64_t groups = (int64_t)sms * 4 * (p.threads / p.G);
-        const int64_t want = (positions + groups - 1) / groups;
-        if (want < p.chain) p.chain = round_chain(p.G, (int)want);
+    if (!tuned) {
+        const int v = regime == kRegimeLatency ? latency_variant(W, positions) : throughput_variant(W, positions);
+        if (v < 0) return fail(UMI_ERR_INVALID_ARG, "no kernel variant for W=" + std::to_string(W));
+        p.variant = v;
+        p.G = t[v].G;
+        p.R = t[v].R;
+        p.threads = (positions > 0 && positions < kSmallCtaBelow) ? 128 : default_threads(p.G);
+        p.chain = chain_cap(p.G);
     }
+    // A band smaller than the chain was sized for gets a shorter chain, so
+    // that its tiles still reach every SM: the rule's chain, or for a plan
+    // tuned at a known band size the rule's chain times the ratio the tuner
+    // preferred at that size (the tuned chain itself at the tuned size).
+    if (positions > 0) {
+        const int rule = std::min(chain_cap(p.G), chain_for(p.G, positions));
+        if (p.tuned_at <= 0) {
+            p.chain = std::min(p.chain, rule);
+        } else if (positions < p.tuned_at) {
+            const int64_t at = std::min(chain_cap(p.G), chain_for(p.G, p.tuned_at));
+            p.chain = std::min(p.chain, chain_at_least(p.G, ((int64_t)rule * p.chain + at - 1) / at));
+        }
+    }
+    p.regime = regime;
     *plan = p;
     return UMI_OK;
 }
@@ -279,17 +380,24 @@ static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const 
 }
 
 // ------------------------------------------------------------- batches --
-umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout)
+umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout,
+                        const BandSizes *plan_sizes)
 {
     int nvar = 0;
     variant_table(&nvar);
     // One band per distinct plan (variant, chain, threads), in descending
     // slot capacity so that the heaviest tiles start first.
-    // Positions per (window length, flavour): a small band gets shorter chains
-    // so that its work still spreads over the whole GPU (make_plan).
-    std::map<std::pair<int, int>, int64_t> band_positions;
+    // Positions per (window length, scale mode) size each band's plan
+    // (make_plan): a small band gets a latency plan and shorter chains so that
+    // its work still spreads over the whole GPU.
+    BandSizes band_positions;
     for (const Curve &c : curves)
         band_positions[std::make_pair(c.W, c.scale_mode)] += c.n;
+    if (plan_sizes)
+        for (auto &kv : band_positions) {
+            auto it = plan_sizes->find(kv.first);
+            if (it != plan_sizes->end()) kv.second = std::max(kv.second, it->second);
+        }
     std::map<std::tuple<int, int, int, int, int>, std::vector<int>> by_plan;
     std::vector<Plan> plans;
     for (size_t b = 0; b < curves.size(); ++b) {
@@ -459,12 +567,13 @@ static void release_pinned(int slot, cudaStream_t stream)
     }
 }
 
-umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream, int *launches)
+umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream, int *launches,
+                              const BandSizes *plan_sizes)
 {
     if (launches) *launches = 0;
     if (curves.empty()) return UMI_OK;
     BatchLayout lay;
-    umi_status st = build_layout(curves, &lay);
+    umi_status st = build_layout(curves, &lay, plan_sizes);
     if (st != UMI_OK) return st;
     if (lay.items.empty()) return UMI_OK;
     for (const auto &band : lay.bands) {
@@ -579,7 +688,8 @@ void count_launches(int n) { g_kernel_launches += n; }
 
 static umi_status batched_impl(const float *flux, const int64_t *offsets, const int32_t *W,
                                int32_t B, const umi_params *params, float *trend, float *detr,
-                               cudaStream_t stream, bool allow_graph)
+                               cudaStream_t stream, bool allow_graph,
+                               const BandSizes *plan_sizes = nullptr)
 {
     clear_error();
     umi_params p;
@@ -604,9 +714,9 @@ static umi_status batched_impl(const float *flux, const int64_t *offsets, const 
         if (n == 0) continue;
         curves.push_back(make_curve(flux + o, trend + o, detr + o, n, W[b], p));
     }
-    if (!allow_graph || !g_graph_enabled.load()) {
+    if (!allow_graph || plan_sizes || !g_graph_enabled.load()) {
         int launches = 0;
-        st = launch_curve_table(curves, stream, &launches);
+        st = launch_curve_table(curves, stream, &launches, plan_sizes);
         g_kernel_launches += launches;
         return st;
     }
@@ -946,6 +1056,10 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
         return fail_cuda(e, "batched host pipeline setup");
     }
     float *dflux = dev, *dtrend = dev + total, *ddetr = dev + 2 * total;
+    // Every chunk is planned from the whole call's bands.
+    BandSizes sizes;
+    for (int32_t b = 0; b < B; ++b)
+        sizes[std::make_pair((int)W_h[b], p.scale_mode)] += offsets_h[b + 1] - offsets_h[b];
     std::vector<int64_t> off_c;
     for (size_t c = 0; c + 1 < cut.size() && st == UMI_OK; ++c) {
         const int32_t b0 = cut[c], b1 = cut[c + 1];
@@ -964,7 +1078,8 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
         }
         off_c.assign(offsets_h + b0, offsets_h + b1 + 1);
         for (auto &x : off_c) x -= o;
-        st = batched_impl(dflux + o, off_c.data(), W_h + b0, b1 - b0, &p, dtrend + o, ddetr + o, cs, false);
+        st = batched_impl(dflux + o, off_c.data(), W_h + b0, b1 - b0, &p, dtrend + o, ddetr + o, cs, false,
+                          &sizes);
         if (st != UMI_OK) break;
         e = cudaEventRecord(ev_done, cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_done, 0);
@@ -1006,7 +1121,18 @@ umi_status umi_get_plan(int32_t W, int64_t positions, umi_plan *out)
     out->chain = p.chain;
     out->threads = p.threads;
     out->variant = p.variant;
+    out->latency = p.regime == kRegimeLatency ? 1 : 0;
     return UMI_OK;
+}
+
+static void plan_out(const Plan &p, umi_plan *out)
+{
+    out->lanes = p.G;
+    out->slots = p.R;
+    out->chain = p.chain;
+    out->threads = p.threads;
+    out->variant = p.variant;
+    out->latency = p.regime == kRegimeLatency ? 1 : 0;
 }
 
 umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *best_out,
@@ -1016,6 +1142,7 @@ umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *be
     if (W < 1 || (W % 2) == 0 || W > kMaxWindow) return fail(UMI_ERR_INVALID_ARG, "bad W");
     if (positions < 1 || positions > (int64_t)1 << 31) return fail(UMI_ERR_INVALID_ARG, "bad positions");
     cudaStream_t s = (cudaStream_t)stream;
+    const int regime = plan_regime(W, positions);
     float *buf = nullptr;
     UMI_CUDA(cudaMalloc((void **)&buf, 3 * sizeof(float) * (size_t)positions), "cudaMalloc");
     fill_noise_kernel<<<1024, 256, 0, s>>>(buf, positions, 0x5eedull + (uint64_t)W);
@@ -1024,27 +1151,37 @@ umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *be
     Plan best;
     double bms = 1e30;
     umi_status st = UMI_OK;
-    // Candidates: every variant whose slot capacity fits W without wasting more
-    // than a third of it (the smallest fitting capacity always qualifies),
-    // two CTA sizes, and chain lengths of about 8 to 136 positions per group.
-    int smallest = 1 << 30;
-    for (int v = 0; v < nv; ++v)
-        if (t[v].G * t[v].R >= W) smallest = std::min(smallest, t[v].G * t[v].R);
+    // Candidates: the variants that waste at most a third of W (the smallest
+    // covering capacity always qualifies) -- in the latency regime also the
+    // 32-lane variants within 2W --, two CTA sizes, and chains of about 8 to
+    // 136 positions plus a third, half, once, twice and three times the chain
+    // the rule gives for this band.
+    const int smallest = smallest_capacity(W);
     for (int v = 0; v < nv && st == UMI_OK; ++v) {
         const int S = t[v].G * t[v].R;
-        if (S < W || (S > smallest && 3 * S > 4 * W)) continue;
+        const bool wide = regime == kRegimeLatency && t[v].G == 32 && S >= W && S <= 2 * W;
+        if (!tight_fit(t[v], W, smallest) && !wide) continue;
         const int G = t[v].G;
+        const int base = chain_for(G, positions);
+        std::vector<int> chains;
+        for (int64_t target : {(int64_t)8, (int64_t)24, (int64_t)40, (int64_t)72, (int64_t)136,
+                               (int64_t)base / 3, (int64_t)base / 2, (int64_t)base, 2 * (int64_t)base,
+                               3 * (int64_t)base}) {
+            const int c = chain_at_least(G, std::max<int64_t>(target, shortest_chain(G)));
+            if (c <= chain_cap(G) + 2 * G && legal_chain(G, c) &&
+                std::find(chains.begin(), chains.end(), c) == chains.end())
+                chains.push_back(c);
+        }
         for (int threads : {128, 256}) {
-            int last_chain = -1;
-            for (int target : {8, 24, 40, 72, 136}) {
+            for (int c : chains) {
                 Plan p;
                 p.variant = v;
                 p.G = G;
                 p.R = t[v].R;
                 p.threads = threads;
-                p.chain = round_chain(G, std::max(G, target));
-                if (p.chain == last_chain || !legal_chain(G, p.chain)) continue;
-                last_chain = p.chain;
+                p.chain = c;
+                p.regime = regime;
+                p.tuned_at = positions;
                 if (p.smem_bytes() > device_info(current_device()).smem_optin) continue;
                 double ms = 0;
                 st = time_plan(p, buf, buf + positions, buf + 2 * positions, positions, W, s, &ms);
@@ -1054,6 +1191,7 @@ umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *be
                     best = p;
                 }
             }
+            if (st != UMI_OK) break;
         }
     }
     cudaFree(buf);
@@ -1061,19 +1199,15 @@ umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *be
     if (best.variant < 0) return fail(UMI_ERR_INVALID_ARG, "no eligible variant");
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[W] = best;
+        g_tuned[std::make_pair((int)W, regime)] = best;
         ++g_tune_epoch;
     }
-    if (best_out) {
-        best_out->lanes = best.G;
-        best_out->slots = best.R;
-        best_out->chain = best.chain;
-        best_out->threads = best.threads;
-        best_out->variant = best.variant;
-    }
+    if (best_out) plan_out(best, best_out);
     if (best_ms) *best_ms = bms;
     return UMI_OK;
 }
+
+static const char *regime_name(int r) { return r == kRegimeLatency ? "latency" : "throughput"; }
 
 umi_status umi_save_tuning(const char *path)
 {
@@ -1085,10 +1219,11 @@ umi_status umi_save_tuning(const char *path)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     int nv = 0;
     const Variant *t = variant_table(&nv);
-    f << "# umi tuning table: gpu|W|G|R|MINB|chain|threads\n";
+    f << "# umi tuning table: gpu|W|regime|G|R|MINB|chain|threads|positions\n";
     for (auto &kv : g_tuned)
-        f << gpu << "|" << kv.first << "|" << kv.second.G << "|" << kv.second.R << "|"
-          << t[kv.second.variant].minb << "|" << kv.second.chain << "|" << kv.second.threads << "\n";
+        f << gpu << "|" << kv.first.first << "|" << regime_name(kv.first.second) << "|" << kv.second.G
+          << "|" << kv.second.R << "|" << t[kv.second.variant].minb << "|" << kv.second.chain << "|"
+          << kv.second.threads << "|" << kv.second.tuned_at << "\n";
     return UMI_OK;
 }
 
@@ -1102,27 +1237,38 @@ umi_status umi_load_tuning(const char *path)
     int nv = 0;
     const Variant *t = variant_table(&nv);
     std::string line;
-    std::map<int, Plan> loaded;
+    std::map<std::pair<int, int>, Plan> loaded;
     while (std::getline(f, line)) {
         if (line.empty() || line[0] == '#') continue;
         std::vector<std::string> parts;
         std::stringstream ss(line);
         std::string tok;
         while (std::getline(ss, tok, '|')) parts.push_back(tok);
-        if (parts.size() != 7 || parts[0] != gpu) continue;
+        // Lines without a regime field are throughput plans; the band size
+        // the plan was tuned at is optional (0: unknown).
+        if (parts.size() == 7) parts.insert(parts.begin() + 2, "throughput");
+        if (parts.size() == 8) parts.push_back("0");
+        if (parts.size() != 9) return fail(UMI_ERR_INVALID_ARG, "bad tuning line: " + line);
+        if (parts[0] != gpu) continue;
+        int regime = -1;
+        if (parts[2] == "throughput") regime = kRegimeThroughput;
+        if (parts[2] == "latency") regime = kRegimeLatency;
         Plan p;
         const int W = std::atoi(parts[1].c_str());
-        p.G = std::atoi(parts[2].c_str());
-        p.R = std::atoi(parts[3].c_str());
-        const int minb = std::atoi(parts[4].c_str());
-        p.chain = std::atoi(parts[5].c_str());
-        p.threads = std::atoi(parts[6].c_str());
+        p.G = std::atoi(parts[3].c_str());
+        p.R = std::atoi(parts[4].c_str());
+        const int minb = std::atoi(parts[5].c_str());
+        p.chain = std::atoi(parts[6].c_str());
+        p.threads = std::atoi(parts[7].c_str());
+        p.regime = regime;
+        p.tuned_at = std::atoll(parts[8].c_str());
         for (int v = 0; v < nv; ++v)
             if (t[v].G == p.G && t[v].R == p.R && t[v].minb == minb) p.variant = v;
-        if (p.variant < 0 || W < 1 || (W % 2) == 0 || W > kMaxWindow || p.G * p.R < W ||
-            !legal_chain(p.G, p.chain) || p.threads < p.G || p.threads > 256 || p.threads % 32)
+        if (regime < 0 || p.variant < 0 || W < 1 || (W % 2) == 0 || W > kMaxWindow || p.G * p.R < W ||
+            !legal_chain(p.G, p.chain) || p.chain > (1 << 20) || p.threads < p.G || p.threads > 256 ||
+            p.threads % 32 || p.tuned_at < 0)
             return fail(UMI_ERR_INVALID_ARG, "bad tuning line: " + line);
-        loaded[W] = p;
+        loaded[std::make_pair(W, regime)] = p;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto &kv : loaded) g_tuned[kv.first] = kv.second;

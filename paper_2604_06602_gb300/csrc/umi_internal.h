@@ -5,6 +5,8 @@
 
 #include <cstdint>
 #include <string>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "umi.h"
@@ -27,12 +29,18 @@ struct DeviceInfo {
 const DeviceInfo &device_info(int device);
 int current_device();
 
+// Planning regimes: a band that fills the GPU at the shortest chain of its
+// throughput variant, and one that does not (see make_plan).
+enum : int { kRegimeThroughput = 0, kRegimeLatency = 1 };
+
 // A launch plan for one window band.
 struct Plan {
     int variant = -1;
     int G = 0, R = 0;
     int chain = 0;    // positions per group
     int threads = 0;  // per CTA
+    int regime = 0;   // kRegimeThroughput or kRegimeLatency
+    int64_t tuned_at = 0;  // band size a tuned plan was measured at (0: unknown)
     // Positions per work item (one warp's tile).
     int tile() const { return (32 / G) * chain; }
     size_t smem_bytes() const
@@ -42,7 +50,11 @@ struct Plan {
 };
 
 bool legal_chain(int G, int chain);
-// Plan for a window length; `positions` sizes the chain when the work is small.
+// Regime of a band of `positions` windows of length W (positions <= 0: throughput).
+int plan_regime(int W, int64_t positions);
+// Plan for a band of `positions` windows of length W (positions <= 0: a band
+// large enough for the longest chain): the tuned plan for (W, regime) if any,
+// else the measured rule; the chain shrinks for small bands.
 umi_status make_plan(int W, int64_t positions, Plan *plan);
 umi_status check_params(const umi_params *p, umi_params *out);
 int resolve_min_valid(int W, int min_valid);
@@ -51,12 +63,19 @@ umi_status prepare_kernel(const Plan &plan, int flavour);
 // Persistent grid size for a plan on the current device.
 int persistent_grid(const Plan &plan, int flavour);
 
+// Windows per (window length, scale mode) band.  A call that runs its
+// curves in several pieces (pipelined chunks, gap segments) plans every piece
+// from the sizes of the whole call's bands, so that it runs the same kernel
+// variants as one batched launch over the same curves.
+using BandSizes = std::map<std::pair<int, int>, int64_t>;
+
 // One batched launch over an explicit curve table (used by the CSR entry
 // point and by the server).  `curves` are host descriptors with device data
 // pointers; device scratch is taken with cudaMallocAsync on `stream`.
-// `launches` (may be null) receives the number of kernels launched.
+// `launches` (may be null) receives the number of kernels launched;
+// `plan_sizes` (may be null: the table's own bands) sizes the plans.
 umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream,
-                              int *launches);
+                              int *launches, const BandSizes *plan_sizes = nullptr);
 
 // Adds to the process-wide count of kernels launched by libumi.
 void count_launches(int n);
@@ -77,7 +96,8 @@ struct BatchLayout {
     std::vector<Band> bands;
     std::vector<Item> items;
 };
-umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout);
+umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout,
+                        const BandSizes *plan_sizes = nullptr);
 
 // A batch planned for caller-owned buffers: `dev_bytes` of device scratch and
 // `host_bytes` of (preferably pinned) host staging for the tables.

@@ -157,6 +157,11 @@ umi_status detrend_segmented(const float *flux, const int64_t *offsets, const in
     if (e != cudaSuccess) return fail_cuda(e, "segment scan");
 
     Bits bits{hbits.data()};
+    // Segments are planned from the whole curves' bands, as the plain batched
+    // call would plan them.
+    BandSizes sizes;
+    for (int32_t b = 0; b < B; ++b)
+        sizes[std::make_pair((int)W[b], p.scale_mode)] += offsets[b + 1] - offsets[b];
     std::vector<Curve> curves;
     std::vector<Segment> segs;
     for (int32_t b = 0; b < B; ++b) {
@@ -183,7 +188,7 @@ umi_status detrend_segmented(const float *flux, const int64_t *offsets, const in
     }
     if (segments_out) *segments_out = (int64_t)curves.size();
     int launches = 0;
-    st = launch_curve_table(curves, stream, &launches);
+    st = launch_curve_table(curves, stream, &launches, &sizes);
     count_launches(launches + 1);
     return st;
 }

@@ -62,7 +62,7 @@ class Params(ctypes.Structure):
 
 class Plan(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("slots", ctypes.c_int32), ("chain", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("variant", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("variant", ctypes.c_int32), ("latency", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -195,14 +195,27 @@ def test_config3_uneven_batch(umi):
     rt, rd = oracle.detrend_batch(b.flux, b.offsets, W)
     compare_trend(tr, rt, what="config3")
     compare_detr(de, rd, what="config3")
-    # Batched output is bit-identical to one launch per curve.
+    # One launch per curve: bit-identical where the curve alone plans to the
+    # same kernel variant as its band in the batch, else the same up to the
+    # rounding of the lane-split sums (the parity tolerance).
+    lens = np.diff(b.offsets)
+    same = differ = 0
     for i in range(0, b.B, 7):
         x = torch.from_numpy(b.curve(i).copy()).cuda()
         t1, d1 = umi.detrend(x, int(W[i]))
         torch.cuda.synchronize()
         s = slice(b.offsets[i], b.offsets[i + 1])
-        assert np.array_equal(t1.cpu().numpy(), tr[s], equal_nan=True)
-        assert np.array_equal(d1.cpu().numpy(), de[s], equal_nan=True)
+        band = umi.get_plan(int(W[i]), int(lens[W == W[i]].sum()))
+        alone = umi.get_plan(int(W[i]), int(lens[i]))
+        if band["variant"] == alone["variant"]:
+            same += 1
+            assert np.array_equal(t1.cpu().numpy(), tr[s], equal_nan=True)
+            assert np.array_equal(d1.cpu().numpy(), de[s], equal_nan=True)
+        else:
+            differ += 1
+            compare_trend(t1.cpu().numpy(), tr[s].astype(np.float64), what="alone vs batch %d" % i)
+            compare_detr(d1.cpu().numpy(), de[s].astype(np.float64), what="alone vs batch %d" % i)
+    assert same > 0 and differ > 0
 
 
 def test_config4_large_window_sampled(umi):
@@ -262,13 +275,89 @@ def test_graph_cache_and_host_entry_point_identical(umi):
     assert np.array_equal(dh.numpy(), d0.cpu().numpy(), equal_nan=True)
 
 
-def test_autotune_keeps_parity(umi):
+def test_autotune_keeps_parity(umi, tmp_path):
     try:
         plan, ms = umi.autotune(361, positions=300000)
-        assert plan["lanes"] * plan["slots"] >= 361 and ms > 0
+        assert plan["lanes"] * plan["slots"] >= 361 and ms > 0 and plan["latency"] == 0
         assert umi.get_plan(361, -1)["chain"] == plan["chain"]
         x = synth.config1().curve(0)
         compare_diag(run_diag(umi, x, 361), oracle.detrend(x, 361), what="tuned")
+        # A single TESS-sized curve is a latency-regime band: tuned separately,
+        # used as tuned at the size it was tuned at, and kept by save/load.
+        small, _ = umi.autotune(361, positions=12500)
+        assert small["latency"] == 1
+        assert umi.get_plan(361, 12500) == small
+        assert umi.get_plan(361, -1)["chain"] == plan["chain"]
+        f = tmp_path / "tuning.txt"
+        umi.save_tuning(str(f))
+        umi.clear_tuning()
+        umi.load_tuning(str(f))
+        assert umi.get_plan(361, 12500) == small
+        assert umi.get_plan(361, -1)["chain"] == plan["chain"]
+        xs = synth.random_curve(91, 12500)
+        compare_diag(run_diag(umi, xs, 361), oracle.detrend(xs, 361), what="tuned latency plan")
+    finally:
+        umi.clear_tuning()
+
+
+def test_plan_rule_choices(umi):
+    """The planner's regimes on this GPU: single curves take a 32-lane
+    variant where one covers W within 2W (every window can start a chain),
+    large bands the smallest covering capacity with long chains."""
+    if torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("thresholds are stated for 152 SMs")
+    umi.clear_tuning()
+    p = umi.get_plan(361, 12500)
+    assert (p["lanes"], p["slots"], p["latency"], p["threads"]) == (32, 12, 1, 128)
+    p = umi.get_plan(361, 18_000_000)
+    assert (p["lanes"], p["slots"], p["latency"], p["chain"], p["threads"]) == (8, 46, 0, 136, 256)
+    p = umi.get_plan(361, 288_000)                     # fills the GPU: throughput, shorter chain
+    assert (p["lanes"], p["latency"]) == (8, 0) and p["chain"] < 136
+    p = umi.get_plan(25, 37000)                        # no 32-lane variant near W = 25
+    assert (p["lanes"], p["slots"], p["latency"]) == (1, 32, 1)
+    assert umi.get_plan(25, 22_000_000)["slots"] == 26
+    p = umi.get_plan(2161, 90000)
+    assert (p["lanes"], p["slots"], p["latency"]) == (32, 68, 0)
+    p = umi.get_plan(721, 30000)
+    assert (p["lanes"], p["slots"], p["latency"]) == (16, 48, 1)
+
+
+def _compiled_variants():
+    import glob
+    import os
+    import re
+    root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2604_06602_gb300", "csrc")
+    out = []
+    for f in sorted(glob.glob(os.path.join(root, "umi_variants_*.cu"))):
+        for m in re.finditer(r"^UMI_DEFINE_VARIANT\((\d+),\s*(\d+),\s*(\d+)\)", open(f).read(), re.M):
+            out.append(tuple(int(v) for v in m.groups()))
+    assert len(out) >= 10
+    return out
+
+
+@pytest.mark.parametrize("variant", _compiled_variants())
+def test_every_variant_forced(umi, tmp_path, variant):
+    """Each compiled variant, forced through a tuning line for both regimes,
+    at its full capacity and at a third of it (the general load path), over
+    several tiles with a ragged tail, against the oracle."""
+    G, R, M = variant
+    S = G * R
+    chain = 5 if G == 32 else 3 * G
+    gpu = torch.cuda.get_device_name()
+    try:
+        for W in sorted({S - 1, max(1, (S // 3) | 1)}):
+            f = tmp_path / "force.txt"
+            f.write_text("".join("%s|%d|%s|%d|%d|%d|%d|128\n" % (gpu, W, r, G, R, M, chain)
+                                 for r in ("throughput", "latency")))
+            umi.clear_tuning()
+            umi.load_tuning(str(f))
+            tile = (32 // G) * chain
+            n = max(16 * tile + 37, 2 * W + 101)
+            pl = umi.get_plan(W, n)
+            assert (pl["lanes"], pl["slots"]) == (G, R)
+            x = synth.random_curve(7000 + S + W, n, nan_runs=2, run_len=(1, W))
+            compare_diag(run_diag(umi, x, W), oracle.detrend(x, W), what="forced %s W=%d" % (variant, W))
     finally:
         umi.clear_tuning()
 
@@ -296,10 +385,13 @@ def test_graph_cache_follows_tuning_changes(umi, tmp_path):
         umi.set_graph_cache(True)
         umi.detrend_batched(flux, b.offsets, W, trend=tr, detr=de)
         launches0 = umi.kernel_launch_count()
+        assert umi.get_plan(361, 48000)["latency"] == 1
+        assert umi.get_plan(361, 48000)["lanes"] == 32
         f = tmp_path / "tune.txt"
-        f.write_text("%s|361|32|12|4|24|128\n" % gpu)
+        f.write_text("%s|361|32|12|4|24|128\n%s|361|latency|16|24|4|16|128\n" % (gpu, gpu))
         umi.load_tuning(str(f))
-        assert umi.get_plan(361, -1)["lanes"] == 32
+        assert umi.get_plan(361, -1)["lanes"] == 32      # a line without regime: throughput
+        assert umi.get_plan(361, 48000)["lanes"] == 16
         umi.detrend_batched(flux, b.offsets, W, trend=tr, detr=de)
         _t.cuda.synchronize()
         ref = oracle.detrend_batch(b.flux, b.offsets, W)[0]

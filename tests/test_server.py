@@ -1,6 +1,8 @@
 """Continuous-batching server on the GPU: each result is the same alone and in
-a mix, admission respects the memory budget, errors are reported per request,
-and injected host-side failures fail only the affected requests."""
+a mix (the batches here stay small enough that every band plans to the same
+kernel variant as the curve alone, so bit for bit), admission respects the
+memory budget, errors are reported per request, and injected host-side
+failures fail only the affected requests."""
 import time
 
 import numpy as np
