@@ -316,7 +316,7 @@ def run_umi(args):
             n_one = int(np.median(batch.lengths[W == w]))
             if n_one > 0 and umi.get_plan(int(w), n_one)["latency"]:
                 umi.autotune(int(w), positions=n_one)
-    tuned_plan = {int(w): umi.get_plan(int(w), -1) for w in sorted(set(W.tolist()))}
+    tuned_plan = {int(w): umi.get_plan(int(w), int(batch.lengths[W == w].sum())) for w in sorted(set(W.tolist()))}
     if args.save_tuning and rank == 0:
         umi.save_tuning(args.save_tuning)
 
