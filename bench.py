@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--tuning-file", default=None,
                     help="load kernel plans from this file instead of running the autotuner")
     ap.add_argument("--save-tuning", default=None, help="write the tuned plans to this file")
+    ap.add_argument("--shard", default="own", choices=["own", "lpt"],
+                    help="own (default): each rank detrends its own batch (weak scaling); "
+                         "lpt: one batch split over the ranks by window work (strong scaling)")
     return ap.parse_args()
 
 
@@ -92,6 +95,15 @@ def max_over_ranks(dist, value, device=None):
     return float(t.item())
 
 
+def sum_over_ranks(dist, value, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def barrier(dist):
     if dist is not None:
         dist.barrier()
@@ -103,9 +115,22 @@ def shard_seed(rank, config=1):
     return synth.BASE_SEED + config + 1000 * rank
 
 
+def lpt_part(batch, W, rank, world):
+    """This rank's part of one batch split over `world` ranks by window work
+    (greedy longest-processing-time): (sub-batch, its W, the part's curve indices)."""
+    from paper_2604_06602_gb300 import partition
+    shards = partition.lpt_shards(partition.window_work(batch.lengths, W), world)
+    idx = shards[rank]
+    return batch.subset(idx), W[idx], idx
+
+
 def make_workload(args, rank):
-    """The synthetic batch of the chosen workload, and a one-line description."""
+    """The synthetic batch of the chosen workload, and a one-line description.
+    With --shard lpt every rank builds the same batch (rank 0's seed) and
+    later keeps its own part of it."""
     from paper_2604_06602_gb300 import synth
+    if getattr(args, "shard", "own") == "lpt":
+        rank = 0
     if args.workload == "c1":
         b = synth.config1(seed=shard_seed(rank, 0))
         return b, "one TESS-like 2-min curve x 18000 samples, W=361"
@@ -295,6 +320,11 @@ def run_umi(args):
 
     batch, desc = make_workload(args, rank)
     W = np.array([umi.window_length(c) for c in batch.cadence], np.int32)
+    global_curves = batch.B * world
+    if args.shard == "lpt":
+        global_curves = batch.B
+        batch, W, _ = lpt_part(batch, W, rank, world)
+        desc += ", split over %d ranks by window work" % world
     evals, samples = window_work(batch.flux, batch.offsets, W)
     flux = torch.from_numpy(batch.flux).to(dev)
     trend = torch.empty_like(flux)
@@ -349,7 +379,7 @@ def run_umi(args):
     elapsed_ms = t_all0.elapsed_time(t_all1)
     kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(starts, ends)]))
     elapsed_ms = max_over_ranks(dist, elapsed_ms, dev)
-    total_evals = evals * world
+    total_evals = sum_over_ranks(dist, evals, dev)
     value = total_evals * args.steps / (elapsed_ms / 1e3)
 
     peaks, peak_src = measured_peaks()
@@ -368,14 +398,15 @@ def run_umi(args):
     line = {
         "metric": "window-evals/s", "value": value, "unit": "window-evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "strong" if args.shard == "lpt" else "weak",
+        "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": desc + ", batched persistent kernel (CUDA graph)",
-                   "global_batch": batch.B * world, "seq_len": int(batch.lengths.max()),
+                   "global_batch": global_curves, "seq_len": int(batch.lengths.max()),
                    "parallelism": "dp%d" % world,
                    "l2": "flushed between steps (%d MB write)" % (flush.numel() * 4 >> 20),
                    "plan": tuned_plan},
-        "curves_per_s": batch.B * world * args.steps / (elapsed_ms / 1e3),
+        "curves_per_s": global_curves * args.steps / (elapsed_ms / 1e3),
         "kernel_ms": kernel_ms,
         "roofline": roofline,
         "clocks": clk,
@@ -557,7 +588,7 @@ def serving_leg(umi, torch, dev, args):
         t = srv.submit(dev_pool[0], Ws[0])
         srv.wait(t, 60)
         srv.release(t)
-        for rate in (1000.0, 5000.0, 20000.0, 50000.0):
+        for rate in (1000.0, 2000.0, 5000.0, 10000.0, 20000.0, 50000.0):
             n = int(min(n_max, max(1000, rate * 0.6)))
             lat, wall, offered = serve_at_rate(umi, srv, dev_pool, Ws, which, arrivals / rate, n)
             st = srv.stats()
@@ -579,7 +610,7 @@ def serving_leg(umi, torch, dev, args):
     torch.cuda.synchronize()
     out["serialized_per_curve_curves_per_s"] = nser / (time.perf_counter() - s0)
     out["serialized_rates"] = []
-    for rate in (1000.0, 5000.0, 20000.0):
+    for rate in (1000.0, 2000.0, 5000.0, 10000.0, 20000.0):
         n = int(min(n_max, max(1000, rate * 0.3)))
         lat, wall = serialized_at_rate(umi, torch, dev_pool, Ws, which, arrivals / rate, n, trend, detr)
         out["serialized_rates"].append({"rate_hz": rate, "requests": n, "curves_per_s": n / wall,

@@ -453,3 +453,32 @@ def test_host_entry_point_pipelined_chunks_identical(umi):
     # Pageable numpy buffers take the same path (copies serialise).
     tn, dn = umi.detrend_batched_host(b.flux, b.offsets, W)
     assert np.array_equal(tn, t0.cpu().numpy(), equal_nan=True)
+
+
+@pytest.mark.parametrize("n,W,parts", [(300000, 2161, 3), (200000, 361, 4)])
+def test_split_long_curve_matches_whole(umi, n, W, parts):
+    """One long curve cut into halo-padded parts, as it would be spread over
+    several GPUs, gives the whole-curve output: bit for bit where a part plans
+    to the same kernel variant as the whole curve, else within the rounding
+    of the lane-split sums."""
+    from paper_2604_06602_gb300 import partition
+    x = synth.random_curve(515 + W, n, nan_runs=3, run_len=(1, 3000))
+    xd = torch.from_numpy(x).cuda()
+    t0, d0 = umi.detrend(xd, W)
+    torch.cuda.synchronize()
+    t0, d0 = t0.cpu().numpy(), d0.cpu().numpy()
+    whole = umi.get_plan(W, n)["variant"]
+    kinds = set()
+    for a, b, lo, hi in partition.split_curve(n, W, parts):
+        t, d = umi.detrend(xd[lo:hi].contiguous(), W)
+        torch.cuda.synchronize()
+        t, d = t.cpu().numpy()[a - lo:b - lo], d.cpu().numpy()[a - lo:b - lo]
+        if umi.get_plan(W, hi - lo)["variant"] == whole:
+            kinds.add("same")
+            assert np.array_equal(t, t0[a:b], equal_nan=True)
+            assert np.array_equal(d, d0[a:b], equal_nan=True)
+        else:
+            kinds.add("differ")
+            compare_trend(t, t0[a:b].astype(np.float64), what="part %d" % a)
+            compare_detr(d, d0[a:b].astype(np.float64), what="part %d" % a)
+    assert kinds == ({"same"} if W == 2161 else {"differ"})
