@@ -134,11 +134,21 @@ umi_status umi_detrend_batched(const float *flux_d, const int64_t *offsets_h, co
  * umi_detrend_batched on HOST buffers: copies flux_h to the device, runs the
  * batched path and copies trend_h / detr_h back, and waits for all of it
  * before returning.  Batches of more than a few million samples are split
- * into up to 8 chunks of whole curves, pipelined over `stream` and two
- * internal copy streams so that copies overlap the detrend; the result does
- * not depend on the chunking.  Device buffers come from cudaMallocAsync on
- * `stream` and are freed before return.  Pinned host memory makes the copies
- * asynchronous DMA; pageable memory works but serialises them.
+ * into up to 8 chunks of whole curves, pipelined over `stream`, a second
+ * compute stream and two copy streams so that copies overlap the detrend;
+ * every chunk is planned from the whole batch's bands, so the result does not
+ * depend on the chunking.  The three side streams and the pipeline's events
+ * belong to the calling host thread: they are created on its first call (per
+ * device) and kept for its later calls.  Device buffers come from
+ * cudaMallocAsync on `stream` and are freed before return.  Pinned host
+ * memory makes the copies asynchronous DMA; pageable memory works but
+ * serialises them.
+ *
+ * Memory pool: the entry points that take cudaMallocAsync scratch raise the
+ * release threshold of the device's default memory pool to its maximum (once
+ * per device), so that freed scratch stays mapped for the next call; the pool
+ * then holds up to the largest scratch one call has taken.  A caller can trim
+ * it with cudaMemPoolTrimTo.
  */
 umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_h,
                                     const int32_t *W_h, int32_t B, const umi_params *params,

@@ -567,6 +567,50 @@ static void release_pinned(int slot, cudaStream_t stream)
     }
 }
 
+// The entry points take their device scratch with cudaMallocAsync from the
+// device's default memory pool.  Its release threshold is raised once per
+// device, so that freed blocks stay in the pool for the next call instead of
+// being unmapped at every synchronisation (with the default threshold of 0 the
+// host entry point's 216 MB buffer for 1000 curves of 18,000 samples was
+// mapped again on every call).  The pool then keeps up to the largest scratch
+// a call has taken.
+void keep_pool_memory()
+{
+    static std::mutex mu;
+    static std::vector<int> done;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done.push_back(dev);
+}
+
+// Side streams and events of the pipelined host entry point, per host thread
+// and device, created on first use and kept (never freed).
+namespace {
+struct HostPipe {
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_c2 = nullptr;
+    std::vector<cudaEvent_t> events;
+};
+thread_local std::map<int, HostPipe> t_pipes;  // intentionally never freed
+}  // namespace
+
+static cudaError_t host_pipe(int dev, HostPipe **out)
+{
+    HostPipe &hp = t_pipes[dev];
+    cudaError_t e = cudaSuccess;
+    if (!hp.s_in) e = cudaStreamCreateWithFlags(&hp.s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !hp.s_out) e = cudaStreamCreateWithFlags(&hp.s_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !hp.s_c2) e = cudaStreamCreateWithFlags(&hp.s_c2, cudaStreamNonBlocking);
+    *out = &hp;
+    return e;
+}
+
 umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream, int *launches,
                               const BandSizes *plan_sizes)
 {
@@ -581,6 +625,7 @@ umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t str
         if (st != UMI_OK) return st;
     }
     const Scratch sc = scratch_layout(curves.size(), lay.items.size(), lay.bands.size());
+    keep_pool_memory();
     // Host staging in one pinned block so a single asynchronous copy moves the tables.
     int slot = 0;
     char *host = nullptr;
@@ -1024,27 +1069,29 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
 
     // Chunks alternate between the caller's stream and a second compute
     // stream, so the next chunk's persistent kernel fills SMs while the
-    // previous one drains.
+    // previous one drains.  The side streams and the events belong to the
+    // calling thread (HostPipe) and are reused by its next call: every use
+    // of them has completed when a call returns.
     cudaStream_t s = (cudaStream_t)stream;
-    cudaStream_t s_in = nullptr, s_out = nullptr, s_c2 = nullptr;
-    std::vector<cudaEvent_t> ev;
-    auto cleanup = [&]() {
-        if (s_in) cudaStreamDestroy(s_in);
-        if (s_out) cudaStreamDestroy(s_out);
-        if (s_c2) cudaStreamDestroy(s_c2);
-        for (cudaEvent_t x : ev) cudaEventDestroy(x);
-    };
+    HostPipe *hp = nullptr;
+    cudaError_t e = host_pipe(current_device(), &hp);
+    if (e != cudaSuccess) return fail_cuda(e, "batched host pipeline streams");
+    cudaStream_t s_in = hp->s_in, s_out = hp->s_out, s_c2 = hp->s_c2;
+    size_t n_ev = 0;
     auto new_event = [&](cudaEvent_t *out) {
-        cudaError_t e = cudaEventCreateWithFlags(out, cudaEventDisableTiming);
-        if (e == cudaSuccess) ev.push_back(*out);
-        return e;
+        if (n_ev == hp->events.size()) {
+            cudaEvent_t x = nullptr;
+            cudaError_t ce = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+            if (ce != cudaSuccess) return ce;
+            hp->events.push_back(x);
+        }
+        *out = hp->events[n_ev++];
+        return cudaSuccess;
     };
     const size_t bytes = sizeof(float) * (size_t)total;
     float *dev = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_c2, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dev, 3 * bytes, s);
+    keep_pool_memory();
+    e = cudaMallocAsync((void **)&dev, 3 * bytes, s);
     cudaEvent_t ev_alloc = nullptr;
     if (e == cudaSuccess) e = new_event(&ev_alloc);
     if (e == cudaSuccess) e = cudaEventRecord(ev_alloc, s);
@@ -1052,7 +1099,6 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
     if (e != cudaSuccess) {
         if (dev) cudaFreeAsync(dev, s);
         cudaStreamSynchronize(s);
-        cleanup();
         return fail_cuda(e, "batched host pipeline setup");
     }
     float *dflux = dev, *dtrend = dev + total, *ddetr = dev + 2 * total;
@@ -1105,7 +1151,6 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
     cudaFreeAsync(dev, s);
     e = cudaStreamSynchronize(s);
     if (st == UMI_OK && e != cudaSuccess) st = fail_cuda(e, "cudaStreamSynchronize");
-    cleanup();
     return st;
 }
 

@@ -80,6 +80,10 @@ umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t str
 // Adds to the process-wide count of kernels launched by libumi.
 void count_launches(int n);
 
+// Raises the release threshold of the current device's default memory pool
+// (once per device), so cudaMallocAsync scratch is reused across calls.
+void keep_pool_memory();
+
 // Gap-split detrend (umi_segments.cu).
 umi_status detrend_segmented(const float *flux, const int64_t *offsets, const int32_t *W, int32_t B,
                              const umi_params *params, const umi_segment_params *seg, float *trend,

@@ -139,6 +139,7 @@ umi_status detrend_segmented(const float *flux, const int64_t *offsets, const in
 
     const int64_t words = (total + 31) / 32;
     unsigned *dbits = nullptr;
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync((void **)&dbits, sizeof(unsigned) * (size_t)words, stream);
     if (e != cudaSuccess) return fail_cuda(e, "cudaMallocAsync (validity bits)");
     const int threads = 256;
