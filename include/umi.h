@@ -382,6 +382,27 @@ const char *umi_version(void);
  * a graph replay counts the kernels it contains).  For launch accounting. */
 long long umi_kernel_launch_count(void);
 
+/*
+ * Checked builds.  The library can be built with UMI_CHECKED
+ * (`python -m paper_2604_06602_gb300.build --checked`, giving
+ * libumi_checked.so): every kernel then checks its shared-memory tile reads,
+ * its work items and its shared-memory size, records each failed check as a
+ * bit in a per-device flag word, and skips the access instead of performing
+ * it.  Bits: 1 = tile slices exceed the launch's dynamic shared memory,
+ * 2 = a tile read outside the warp's slice, 4 = a work item naming a curve
+ * outside the table, 8 = a work item whose tile starts past its curve's end.
+ * A checked build allocates one 4-byte flag word per device on first use
+ * (so umi_detrend_batched_noalloc allocates once there).  The paper has no
+ * counterpart; this stands in for a memory checker on GPUs where none runs.
+ *
+ * umi_checked_build: 1 in a checked build, 0 otherwise.
+ * umi_check_flags: synchronises the current device, stores its flag word in
+ * *flags and clears it when `clear` is nonzero.  In a normal build it returns
+ * UMI_ERR_INVALID_ARG (no checks ran, so there is nothing to report).
+ */
+int32_t umi_checked_build(void);
+umi_status umi_check_flags(uint32_t *flags, int32_t clear);
+
 #ifdef __cplusplus
 }
 #endif

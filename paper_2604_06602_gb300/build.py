@@ -18,6 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build", platform.machine())
 LIB = os.path.join(PKG, "libumi.so")
 STAMP = LIB + ".arch"
+# The checked build (UMI_CHECKED: index checks in every kernel, see umi.h).
+CHECKED_LIB = os.path.join(PKG, "libumi_checked.so")
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -45,26 +47,35 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
+def _paths(checked: bool):
+    lib = CHECKED_LIB if checked else LIB
+    return lib, lib + ".arch", BUILD + ("-checked" if checked else "")
+
+
+def up_to_date(checked: bool = False) -> bool:
+    lib, stamp, _ = _paths(checked)
+    if not (os.path.exists(lib) and os.path.exists(stamp)):
         return False
-    if open(STAMP).read().strip() != platform.machine():
+    if open(stamp).read().strip() != platform.machine():
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile and link libumi.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          checked: bool = False) -> str:
+    """Compile and link libumi.so (libumi_checked.so with `checked`); returns its path."""
+    lib, stamp, bdir = _paths(checked)
+    if not force and up_to_date(checked):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     srcs = sources()
+    extra = ["-DUMI_CHECKED"] if checked else []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc] + ARCH_FLAGS + CFLAGS + ["-c", src, "-o", obj]
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
+        cmd = [cc] + ARCH_FLAGS + CFLAGS + extra + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -79,17 +90,17 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         for _, log in results:
             print(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [cc] + ARCH_FLAGS + ["-shared", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    with open(STAMP, "w") as f:
+    os.replace(tmp, lib)
+    with open(stamp, "w") as f:
         f.write(platform.machine() + "\n")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

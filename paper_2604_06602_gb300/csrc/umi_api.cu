@@ -289,11 +289,47 @@ umi_status check_params(const umi_params *p, umi_params *out)
 
 static std::mutex g_attr_mu;
 
+// ---------------------------------------------------------- checked build --
+// Builds compiled with UMI_CHECKED give every launch a device flag word (one
+// per device, allocated by prepare_kernel, which runs before any launch or
+// graph capture); the kernel sets a bit for each failed index check and skips
+// the access.  Normal builds pass no word and compile no checks.
+#ifdef UMI_CHECKED
+static std::mutex g_check_mu;
+static std::map<int, uint32_t *> g_check_words;
+
+static uint32_t *check_word()
+{
+    std::lock_guard<std::mutex> lk(g_check_mu);
+    auto it = g_check_words.find(current_device());
+    return it == g_check_words.end() ? nullptr : it->second;
+}
+
+static umi_status ensure_check_word()
+{
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_check_mu);
+    if (g_check_words.count(dev)) return UMI_OK;
+    uint32_t *w = nullptr;
+    UMI_CUDA(cudaMalloc((void **)&w, sizeof(uint32_t)), "cudaMalloc (check flags)");
+    UMI_CUDA(cudaMemset(w, 0, sizeof(uint32_t)), "cudaMemset (check flags)");
+    g_check_words[dev] = w;
+    return UMI_OK;
+}
+#else
+static uint32_t *check_word() { return nullptr; }
+static umi_status ensure_check_word() { return UMI_OK; }
+#endif
+
 umi_status prepare_kernel(const Plan &plan, int flavour)
 {
     int n = 0;
     const Variant *t = variant_table(&n);
     if (plan.variant < 0 || plan.variant >= n) return fail(UMI_ERR_INVALID_ARG, "bad plan");
+    {
+        const umi_status cst = ensure_check_word();
+        if (cst != UMI_OK) return cst;
+    }
     const size_t smem = plan.smem_bytes();
     const DeviceInfo &di = device_info(current_device());
     if (smem > di.smem_optin)
@@ -369,6 +405,8 @@ static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const 
     a.chain = plan.chain;
     a.queue = nullptr;
     if (diag) a.diag = *diag;
+    a.n_curves = 0;
+    a.check = check_word();
     int nv = 0;
     const Variant *t = variant_table(&nv);
     LaunchFn fn = t[plan.variant].launch[flavour];
@@ -411,6 +449,7 @@ umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout,
     }
     layout->bands.clear();
     layout->items.clear();
+    layout->n_curves = (int32_t)curves.size();
     for (auto &kv : by_plan) {
         BatchLayout::Band band;
         band.plan = plans[kv.second.front()];
@@ -469,6 +508,8 @@ static umi_status enqueue_bands(const BatchLayout &lay, char *dev, const Scratch
         a.n_items = band.n_items;
         a.chain = band.plan.chain;
         a.queue = reinterpret_cast<int32_t *>(dev + sc.counter_off) + k;
+        a.n_curves = lay.n_curves;
+        a.check = check_word();
         const int warps = band.plan.threads / 32;
         const int grid =
             std::min((band.n_items + warps - 1) / warps, persistent_grid(band.plan, band.flavour));
@@ -843,6 +884,7 @@ static umi_status time_plan(const Plan &plan, const float *flux, float *trend, f
     umi_default_params(&p);
     std::vector<Curve> curves{make_curve(flux, trend, detr, n, W, p)};
     BatchLayout lay;
+    lay.n_curves = 1;
     lay.bands.resize(1);
     lay.bands[0].plan = plan;
     lay.bands[0].first_item = 0;
@@ -1340,5 +1382,32 @@ void umi_set_graph_cache(int enabled)
 
 // Number of kernels this library has launched in the process (for reports).
 long long umi_kernel_launch_count(void) { return g_kernel_launches.load(); }
+
+int32_t umi_checked_build(void)
+{
+#ifdef UMI_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+umi_status umi_check_flags(uint32_t *flags, int32_t clear)
+{
+    clear_error();
+    if (!flags) return fail(UMI_ERR_INVALID_ARG, "null flags");
+    *flags = 0;
+#ifdef UMI_CHECKED
+    UMI_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    uint32_t *w = check_word();
+    if (!w) return UMI_OK;  // nothing has launched on this device yet
+    UMI_CUDA(cudaMemcpy(flags, w, sizeof(uint32_t), cudaMemcpyDeviceToHost), "cudaMemcpy (check flags)");
+    if (clear) UMI_CUDA(cudaMemset(w, 0, sizeof(uint32_t)), "cudaMemset (check flags)");
+    return UMI_OK;
+#else
+    (void)clear;
+    return fail(UMI_ERR_INVALID_ARG, "library built without UMI_CHECKED: no index checks ran");
+#endif
+}
 
 }  // extern "C"

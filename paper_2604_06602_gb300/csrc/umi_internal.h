@@ -99,6 +99,7 @@ struct BatchLayout {
     };
     std::vector<Band> bands;
     std::vector<Item> items;
+    int32_t n_curves = 0;  // entries of the curve table the items index
 };
 umi_status build_layout(const std::vector<Curve> &curves, BatchLayout *layout,
                         const BandSizes *plan_sizes = nullptr);

@@ -78,6 +78,39 @@ struct LaunchArgs {
     int32_t chain;        // P: consecutive positions per group
     int32_t *queue;       // persistent work counter, or nullptr: one item per CTA
     Diag diag;
+    int32_t n_curves;     // entries of `curves` (checked builds test item indices)
+    uint32_t *check;      // checked builds: flag word of failed index checks
+};
+
+// Index checks of the checked build (compiled with UMI_CHECKED).  A failed
+// check sets its bit in LaunchArgs::check and the access is skipped (a read
+// gives kGap, a write is dropped), so a bad index is reported, never
+// performed.  Normal builds compile none of it.
+enum : uint32_t {
+    kCheckSmemSize = 1u << 0,    // the warps' tile slices exceed the launch's dynamic smem
+    kCheckTileRead = 1u << 1,    // window, slide or centre read outside the warp's tile
+    kCheckCurveIndex = 1u << 2,  // work item names a curve outside the table
+    kCheckItemTile = 1u << 3,    // work item's tile starts past its curve's end
+};
+
+// Read-only view of a warp's tile: a bare pointer in normal builds, a
+// bounds-checked reader in checked builds.
+struct TileRef {
+    const float *p;
+#ifdef UMI_CHECKED
+    int len;
+    uint32_t *check;
+    __device__ __forceinline__ float operator[](int i) const
+    {
+        if (i < 0 || i >= len) {
+            if (check) atomicOr(check, kCheckTileRead);
+            return kGap;
+        }
+        return p[i];
+    }
+#else
+    __device__ __forceinline__ float operator[](int i) const { return p[i]; }
+#endif
 };
 
 // ---- group-wide reductions over G aligned lanes --------------------------
@@ -179,18 +212,18 @@ __device__ __forceinline__ float key_float(unsigned k)
 // opaque register so the compiler does not keep R loop-invariant predicates
 // alive across the chain.
 template <int G, int R>
-__device__ __forceinline__ void load_window(float2 (&x)[R / 2], const float *tile, int q, int glane,
+__device__ __forceinline__ void load_window(float2 (&x)[R / 2], const TileRef tile, int q, int glane,
                                             int W, bool tail_only)
 {
-    const float *base = tile + q + glane;
+    const int base = q + glane;
     if (tail_only) {
 #pragma unroll
         for (int k = 0; k < R / 2 - 1; ++k) {
-            x[k].x = base[G * (2 * k)];
-            x[k].y = base[G * (2 * k + 1)];
+            x[k].x = tile[base + G * (2 * k)];
+            x[k].y = tile[base + G * (2 * k + 1)];
         }
-        const float a = base[G * (R - 2)];
-        const float b = base[G * (R - 1)];
+        const float a = tile[base + G * (R - 2)];
+        const float b = tile[base + G * (R - 1)];
         x[R / 2 - 1].x = (glane + G * (R - 2) < W) ? a : kGap;
         x[R / 2 - 1].y = (glane + G * (R - 1) < W) ? b : kGap;
     } else {
@@ -198,8 +231,8 @@ __device__ __forceinline__ void load_window(float2 (&x)[R / 2], const float *til
         asm volatile("" : "+r"(lim));
 #pragma unroll
         for (int k = 0; k < R / 2; ++k) {
-            const float a = base[G * (2 * k)];
-            const float b = base[G * (2 * k + 1)];
+            const float a = tile[base + G * (2 * k)];
+            const float b = tile[base + G * (2 * k + 1)];
             x[k].x = (G * (2 * k) < lim) ? a : kGap;
             x[k].y = (G * (2 * k + 1) < lim) ? b : kGap;
         }
@@ -220,7 +253,7 @@ struct MedianState {
 enum : int { kFlagDiag = 1, kFlagMad = 2 };
 
 template <int G, int R, int FLAGS>
-__device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, const float *tile,
+__device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, const TileRef tile,
                                               int64_t t0, int q0, int P, int glane)
 {
     constexpr int S = G * R;
@@ -289,13 +322,13 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             // Bitwise binary search for the key of rank `target` among the S
             // slots.  It reads the window from shared memory (it runs once per
             // chain), which keeps the register arrays free for the hot loops.
-            const float *wb = tile + q + glane;
+            const int wb = q + glane;
             int lim = W - glane;
             asm volatile("" : "+r"(lim));
             unsigned lo = 0xffffffffu, hi = 0u;
 #pragma unroll 4
             for (int i = 0; i < R; ++i) {
-                const float v = wb[G * i];
+                const float v = tile[wb + G * i];
                 const bool valid = (G * i < lim) && (v > kGapLimit);
                 const unsigned kk = float_key(v);
                 lo = valid ? min(lo, kk) : lo;
@@ -314,7 +347,7 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                 int c = 0;
 #pragma unroll 4
                 for (int i = 0; i < R; ++i) {
-                    const float v = (G * i < lim) ? wb[G * i] : kGap;
+                    const float v = (G * i < lim) ? tile[wb + G * i] : kGap;
                     c += (float_key(v) < cand) ? 1 : 0;
                 }
                 c = group_sum_int<G>(c);
@@ -501,6 +534,19 @@ __global__ void __launch_bounds__(256, MINB) umi_tile_kernel(LaunchArgs a)
     const int T = (32 / G) * P;
     const int tile_len = T + S - 1;
     float *tile = smem + (size_t)warp * tile_len;
+#ifdef UMI_CHECKED
+    {
+        unsigned dsm;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+        if ((uint64_t)n_warps * (uint64_t)tile_len * sizeof(float) > dsm) {
+            if (threadIdx.x == 0 && a.check) atomicOr(a.check, kCheckSmemSize);
+            return;
+        }
+    }
+    const TileRef tref{tile, tile_len, a.check};
+#else
+    const TileRef tref{tile};
+#endif
 
     int item = blockIdx.x * n_warps + warp;
     for (;;) {
@@ -511,9 +557,23 @@ __global__ void __launch_bounds__(256, MINB) umi_tile_kernel(LaunchArgs a)
         }
         if (item >= a.n_items) break;
         const Item wi = a.items ? a.items[item] : Item{0, item};
+#ifdef UMI_CHECKED
+        if (a.curves && (wi.curve < 0 || wi.curve >= a.n_curves)) {
+            if (lane == 0 && a.check) atomicOr(a.check, kCheckCurveIndex);
+            if (!a.queue) break;
+            continue;
+        }
+#endif
         const Curve cv = a.curves ? a.curves[wi.curve] : a.single;
         const int64_t t0 = (int64_t)wi.tile * T;
         const int h = (cv.W - 1) >> 1;
+#ifdef UMI_CHECKED
+        if (wi.tile < 0 || t0 >= (cv.n > 0 ? cv.n : 1)) {
+            if (lane == 0 && a.check) atomicOr(a.check, kCheckItemTile);
+            if (!a.queue) break;
+            continue;
+        }
+#endif
 
         for (int k = lane; k < tile_len; k += 32) {
             const int64_t idx = t0 - h + k;
@@ -525,7 +585,7 @@ __global__ void __launch_bounds__(256, MINB) umi_tile_kernel(LaunchArgs a)
             tile[k] = v;
         }
         __syncwarp();
-        process_chain<G, R, FLAGS>(cv, a.diag, tile, t0, group * P, P, glane);
+        process_chain<G, R, FLAGS>(cv, a.diag, tref, t0, group * P, P, glane);
         __syncwarp();  // every lane is done with the tile before it is restaged
         if (!a.queue) break;
     }

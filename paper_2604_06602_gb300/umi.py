@@ -41,7 +41,7 @@ EXPORTS = [
     "umi_server_poll", "umi_server_wait", "umi_server_copy_out", "umi_server_release",
     "umi_server_get_stats", "umi_server_inject_fault", "umi_server_destroy", "umi_last_error",
     "umi_version", "umi_kernel_launch_count", "umi_default_segment_params",
-    "umi_detrend_segmented",
+    "umi_detrend_segmented", "umi_checked_build", "umi_check_flags",
 ]
 
 
@@ -145,6 +145,8 @@ def load(build_if_missing: bool = False):
             "umi_last_error": (ctypes.c_char_p, []),
             "umi_version": (ctypes.c_char_p, []),
             "umi_kernel_launch_count": (ctypes.c_longlong, []),
+            "umi_checked_build": (_i32, []),
+            "umi_check_flags": (ctypes.c_int, [P(ctypes.c_uint32), _i32]),
             "umi_default_segment_params": (None, [P(SegmentParams)]),
             "umi_detrend_segmented": (ctypes.c_int, [_vp, _vp, _vp, _i32, P(Params), P(SegmentParams),
                                                      _vp, _vp, P(ctypes.c_int64), _vp]),
@@ -188,6 +190,18 @@ def version() -> str:
 
 def kernel_launch_count() -> int:
     return int(load().umi_kernel_launch_count())
+
+
+def checked_build() -> bool:
+    """True when the loaded library is the UMI_CHECKED build."""
+    return bool(load().umi_checked_build())
+
+
+def check_flags(clear=False) -> int:
+    """Checked builds: the current device's flag word of failed index checks."""
+    f = ctypes.c_uint32()
+    _check(load().umi_check_flags(ctypes.byref(f), int(bool(clear))))
+    return int(f.value)
 
 
 def _stream_handle(stream):

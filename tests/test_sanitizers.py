@@ -1,0 +1,33 @@
+"""Host-side memory and undefined-behaviour checks: the C oracle built with
+AddressSanitizer and UndefinedBehaviorSanitizer, driven over its edge cases
+(compute-sanitizer is not available for the GPU side; the kernels' own
+checked build covers that, see test_checked_build.py)."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_oracle_under_asan_and_ubsan(tmp_path):
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("gcc not available")
+    exe = tmp_path / "oracle_sanitize"
+    cmd = [cc, "-std=c11", "-O1", "-g", "-fno-omit-frame-pointer",
+           "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined",
+           os.path.join(ROOT, "oracle", "umi_oracle.c"),
+           os.path.join(ROOT, "tests", "oracle_sanitize_driver.c"),
+           "-o", str(exe), "-lpthread", "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0 and "sanitize" in r.stderr and "cannot find" in r.stderr:
+        pytest.skip("sanitizer runtime not installed")
+    assert r.returncode == 0, r.stderr
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=1:abort_on_error=0",
+               UBSAN_OPTIONS="print_stacktrace=1:halt_on_error=1")
+    r = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, (r.stdout, r.stderr[-4000:])
+    assert "runtime error" not in r.stderr and "AddressSanitizer" not in r.stderr
+    assert "0 failures" in r.stdout
