@@ -513,8 +513,15 @@ def e2e_leg(umi, torch, batch, W, evals, args):
 def serve_at_rate(umi, srv, dev_pool, Ws, which, arrivals, n):
     """Submits n requests on the Poisson schedule; returns latencies [s],
     wall time and the offered rate actually achieved."""
-    lat, pending = [], []
+    lat, phases, pending = [], [], []
     t0 = time.perf_counter()
+
+    def finish(tt):
+        tl = srv.timeline(tt)
+        lat.append(tl["done"])
+        phases.append((tl["admit"], tl["launch"], tl["done"]))
+        srv.release(tt)
+
     for i in range(n):
         due = t0 + arrivals[i]
         while True:
@@ -526,17 +533,14 @@ def serve_at_rate(umi, srv, dev_pool, Ws, which, arrivals, n):
         k = int(which[i])
         pending.append(srv.submit(dev_pool[k], Ws[k]))
         while pending:
-            res = srv.poll(pending[0])
-            if res is None:
+            if srv.poll(pending[0]) is None:
                 break
-            lat.append(res[2])
-            srv.release(pending.pop(0))
+            finish(pending.pop(0))
     t_sub = time.perf_counter() - t0
     for tt in pending:
         srv.wait(tt, 120)
-        lat.append(srv.poll(tt)[2])
-        srv.release(tt)
-    return np.array(lat), time.perf_counter() - t0, n / t_sub
+        finish(tt)
+    return np.array(lat), time.perf_counter() - t0, n / t_sub, np.array(phases)
 
 
 def serialized_at_rate(umi, torch, dev_pool, Ws, which, arrivals, n, trend, detr):
@@ -590,12 +594,17 @@ def serving_leg(umi, torch, dev, args):
         srv.release(t)
         for rate in (1000.0, 2000.0, 5000.0, 10000.0, 20000.0, 50000.0):
             n = int(min(n_max, max(1000, rate * 0.6)))
-            lat, wall, offered = serve_at_rate(umi, srv, dev_pool, Ws, which, arrivals / rate, n)
+            lat, wall, offered, ph = serve_at_rate(umi, srv, dev_pool, Ws, which, arrivals / rate, n)
             st = srv.stats()
             out["rates"].append({"rate_hz": rate, "offered_hz": offered, "requests": n,
                                  "curves_per_s": n / wall,
                                  "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                                 "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+                                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                                 # medians of submit->admit, admit->launch, launch->done
+                                 "p50_phases_ms": {
+                                     "queued": float(np.median(ph[:, 0]) * 1e3),
+                                     "batching": float(np.median(ph[:, 1] - ph[:, 0]) * 1e3),
+                                     "gpu": float(np.median(ph[:, 2] - ph[:, 1]) * 1e3)}})
         out["mean_batch_curves"] = st["mean_batch_curves"]
         out["batches"] = st["batches_launched"]
     # Serialized per-curve launches of the same request stream, one stream.

@@ -350,6 +350,16 @@ umi_status umi_server_submit(umi_server *s, const float *flux, int is_device_ptr
 umi_status umi_server_poll(umi_server *s, uint64_t ticket, const float **trend_d,
                            const float **detr_d, double *latency_s);
 
+/*
+ * Timeline of a finished request, in seconds after its submit (host clock):
+ * admitted (memory reserved), launched (its batch handed to the GPU) and
+ * done (the batch's completion seen by the scheduler; equals *latency_s of
+ * umi_server_poll).  Any pointer may be NULL.  UMI_ERR_NOT_READY before the
+ * request is done; UMI_ERR_FAILED / UMI_ERR_UNKNOWN_TICKET as for poll.
+ */
+umi_status umi_server_timeline(umi_server *s, uint64_t ticket, double *admit_s, double *launch_s,
+                               double *done_s);
+
 /* Blocks until the ticket is done or failed, or timeout_s passes. */
 umi_status umi_server_wait(umi_server *s, uint64_t ticket, double timeout_s);
 

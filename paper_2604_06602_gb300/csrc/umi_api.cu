@@ -378,6 +378,7 @@ static Curve make_curve(const float *flux, float *trend, float *detr, int64_t n,
 static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const umi_params *params,
                                  float *trend, float *detr, const Diag *diag, cudaStream_t stream)
 {
+    NvtxRange nvtx("umi detrend");
     clear_error();
     umi_params p;
     umi_status st = check_params(params, &p);
@@ -732,6 +733,7 @@ static void destroy_entry(GraphEntry &g)
 
 static umi_status build_graph(const std::vector<Curve> &curves, GraphEntry *g)
 {
+    NvtxRange nvtx("umi graph capture");
     BatchLayout lay;
     umi_status st = build_layout(curves, &lay);
     if (st != UMI_OK) return st;
@@ -777,6 +779,7 @@ static umi_status batched_impl(const float *flux, const int64_t *offsets, const 
                                cudaStream_t stream, bool allow_graph,
                                const BandSizes *plan_sizes = nullptr)
 {
+    NvtxRange nvtx("umi detrend batched");
     clear_error();
     umi_params p;
     umi_status st = check_params(params, &p);
@@ -953,6 +956,7 @@ static umi_status noalloc_batched(const float *flux, const int64_t *offsets, con
                                   int32_t B, const umi_params *params, float *trend, float *detr,
                                   cudaStream_t stream)
 {
+    NvtxRange nvtx("umi detrend batched noalloc");
     clear_error();
     umi_params p;
     umi_status st = check_params(params, &p);
@@ -1078,6 +1082,7 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
                                     const int32_t *W_h, int32_t B, const umi_params *params,
                                     float *trend_h, float *detr_h, void *stream)
 {
+    NvtxRange nvtx("umi detrend batched host");
     clear_error();
     if (B < 0 || (B > 0 && (!offsets_h || !W_h))) return fail(UMI_ERR_INVALID_ARG, "bad batch");
     if (B == 0) return UMI_OK;
@@ -1225,6 +1230,7 @@ static void plan_out(const Plan &p, umi_plan *out)
 umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *best_out,
                         double *best_ms)
 {
+    NvtxRange nvtx("umi autotune");
     clear_error();
     if (W < 1 || (W % 2) == 0 || W > kMaxWindow) return fail(UMI_ERR_INVALID_ARG, "bad W");
     if (positions < 1 || positions > (int64_t)1 << 31) return fail(UMI_ERR_INVALID_ARG, "bad positions");

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -79,6 +80,15 @@ umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t str
 
 // Adds to the process-wide count of kernels launched by libumi.
 void count_launches(int n);
+
+// A named NVTX range over a scope, for profilers (NVTX 3 is header-only and
+// costs a branch when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Raises the release threshold of the current device's default memory pool
 // (once per device), so cudaMallocAsync scratch is reused across calls.

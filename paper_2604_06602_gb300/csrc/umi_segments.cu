@@ -116,6 +116,7 @@ umi_status detrend_segmented(const float *flux, const int64_t *offsets, const in
                              const umi_params *params, const umi_segment_params *seg, float *trend,
                              float *detr, int64_t *segments_out, cudaStream_t stream)
 {
+    NvtxRange nvtx("umi detrend segmented");
     clear_error();
     if (segments_out) *segments_out = 0;
     umi_params p;

@@ -100,7 +100,7 @@ struct Request {
     float *flux = nullptr, *trend = nullptr, *detr = nullptr;
     bool admitted_mem = false;       // owns its arena range
     ReqState state = ReqState::Queued;
-    double t_submit = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_launch = 0, t_done = 0;  // host clock, seconds
 };
 
 struct Batch {
@@ -207,6 +207,7 @@ static void admit_locked(umi_server *s)
         }
         r.admitted_mem = true;
         r.state = ReqState::Admitted;
+        r.t_admit = now_s();
         s->resident_slots++;
         s->stats.admitted++;
         s->stats.resident_bytes = s->alloc->used();
@@ -261,6 +262,7 @@ static void fail_requests_locked(umi_server *s, const std::vector<uint64_t> &tic
 // enqueuing device work.
 static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mutex> &lk)
 {
+    NvtxRange nvtx("umi server batch launch");
     const size_t take = std::min<size_t>(s->admitted.size(), (size_t)s->cfg.max_batch_curves);
     std::vector<uint64_t> tickets(s->admitted.begin(), s->admitted.begin() + take);
     s->admitted.erase(s->admitted.begin(), s->admitted.begin() + take);
@@ -274,9 +276,11 @@ static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mute
     };
     std::vector<Job> jobs;
     jobs.reserve(take);
+    const double t_launch = now_s();
     for (uint64_t t : tickets) {
         Request &r = *s->reqs[t];
         r.state = ReqState::Running;
+        r.t_launch = t_launch;
         Job j{r.flux, r.trend, r.detr, r.dev_src, std::move(r.host_copy), r.n, r.W, r.params};
         r.host_copy = std::vector<float>();
         jobs.push_back(std::move(j));
@@ -526,6 +530,23 @@ umi_status umi_server_poll(umi_server *s, uint64_t ticket, const float **trend_d
     if (trend_d) *trend_d = r.trend;
     if (detr_d) *detr_d = r.detr;
     if (latency_s) *latency_s = r.t_done - r.t_submit;
+    return UMI_OK;
+}
+
+umi_status umi_server_timeline(umi_server *s, uint64_t ticket, double *admit_s, double *launch_s,
+                               double *done_s)
+{
+    clear_error();
+    if (!s) return fail(UMI_ERR_INVALID_ARG, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(UMI_ERR_UNKNOWN_TICKET, "unknown ticket");
+    const Request &r = *it->second;
+    if (r.state == ReqState::Failed) return fail(UMI_ERR_FAILED, "request failed");
+    if (r.state != ReqState::Done) return UMI_ERR_NOT_READY;
+    if (admit_s) *admit_s = r.t_admit - r.t_submit;
+    if (launch_s) *launch_s = r.t_launch - r.t_submit;
+    if (done_s) *done_s = r.t_done - r.t_submit;
     return UMI_OK;
 }
 

@@ -41,7 +41,7 @@ EXPORTS = [
     "umi_server_poll", "umi_server_wait", "umi_server_copy_out", "umi_server_release",
     "umi_server_get_stats", "umi_server_inject_fault", "umi_server_destroy", "umi_last_error",
     "umi_version", "umi_kernel_launch_count", "umi_default_segment_params",
-    "umi_detrend_segmented", "umi_checked_build", "umi_check_flags",
+    "umi_detrend_segmented", "umi_checked_build", "umi_check_flags", "umi_server_timeline",
 ]
 
 
@@ -137,6 +137,8 @@ def load(build_if_missing: bool = False):
                                                  P(ctypes.c_uint64)]),
             "umi_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, P(_vp), P(_vp), P(ctypes.c_double)]),
             "umi_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double]),
+            "umi_server_timeline": (ctypes.c_int, [_vp, ctypes.c_uint64, P(ctypes.c_double),
+                                                   P(ctypes.c_double), P(ctypes.c_double)]),
             "umi_server_copy_out": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, _vp]),
             "umi_server_release": (ctypes.c_int, [_vp, ctypes.c_uint64]),
             "umi_server_get_stats": (ctypes.c_int, [_vp, P(ServerStats)]),
@@ -428,6 +430,15 @@ class Server:
 
     def wait(self, ticket, timeout_s=60.0):
         _check(load().umi_server_wait(self._h, ticket, float(timeout_s)))
+
+    def timeline(self, ticket):
+        """None while not ready, else seconds after submit: {admit, launch, done}."""
+        a, l, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        st = load().umi_server_timeline(self._h, ticket, ctypes.byref(a), ctypes.byref(l), ctypes.byref(d))
+        if st == UMI_ERR_NOT_READY:
+            return None
+        _check(st)
+        return {"admit": a.value, "launch": l.value, "done": d.value}
 
     def copy_out(self, ticket, n):
         trend = np.empty(n, np.float32)

@@ -77,10 +77,14 @@ def test_device_inputs_and_poll_pointers(umi):
         srv.wait(t, 60.0)
         tr_ptr, de_ptr, lat = srv.poll(t)
         assert tr_ptr and de_ptr and lat > 0
+        tl = srv.timeline(t)
+        assert 0 <= tl["admit"] <= tl["launch"] <= tl["done"] and tl["done"] == lat
         tr, _ = srv.copy_out(t, x.size)
         ta, _ = alone(umi, x, 361)
         assert np.array_equal(tr, ta, equal_nan=True)
         srv.release(t)
+        with pytest.raises(umi.UmiError):
+            srv.timeline(t)                               # released: unknown ticket
 
 
 def test_budget_backpressure(umi):
