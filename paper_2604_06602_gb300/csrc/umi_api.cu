@@ -114,7 +114,7 @@ static int default_threads(int G) { return G <= 2 ? 128 : 256; }
 //  * below kSmallCtaBelow positions 128-thread CTAs spread a band more evenly.
 static const int kWarpsPerSm = 16;
 static const int kLatencyItemsPerSm = 32;
-static const int64_t kRegisterRichBelow = 3000000;
+static const int64_t kRegisterRichBelow = 500000;
 static const int64_t kSmallCtaBelow = 300000;
 
 // Tuned plans, keyed by (window length, regime) (filled by umi_autotune /
