@@ -124,6 +124,18 @@ def lpt_part(batch, W, rank, world):
     return batch.subset(idx), W[idx], idx
 
 
+def tune_for_batch(umi, batch, W):
+    """The kernel plans the benchmark times: for each window length, tuned at
+    about the batch's own size (the best chain length depends on it), and,
+    where one curve alone is a latency-regime band, at a median curve."""
+    for w in sorted(set(W.tolist())):
+        n_w = int(batch.lengths[W == w].sum())
+        umi.autotune(int(w), positions=max(1_000_000, min(n_w, 20_000_000)))
+        n_one = int(np.median(batch.lengths[W == w]))
+        if n_one > 0 and umi.get_plan(int(w), n_one)["latency"]:
+            umi.autotune(int(w), positions=n_one)
+
+
 def make_workload(args, rank):
     """The synthetic batch of the chosen workload, and a one-line description.
     With --shard lpt every rank builds the same batch (rank 0's seed) and
@@ -338,14 +350,7 @@ def run_umi(args):
     if args.tuning_file:
         umi.load_tuning(args.tuning_file)
     else:
-        for w in sorted(set(W.tolist())):
-            # Tune at about the batch's own size (the best chain length depends on it),
-            # and, where one curve alone is a latency-regime band, at a median curve.
-            n_w = int(batch.lengths[W == w].sum())
-            umi.autotune(int(w), positions=max(1_000_000, min(n_w, 20_000_000)))
-            n_one = int(np.median(batch.lengths[W == w]))
-            if n_one > 0 and umi.get_plan(int(w), n_one)["latency"]:
-                umi.autotune(int(w), positions=n_one)
+        tune_for_batch(umi, batch, W)
     tuned_plan = {int(w): umi.get_plan(int(w), int(batch.lengths[W == w].sum())) for w in sorted(set(W.tolist()))}
     if args.save_tuning and rank == 0:
         umi.save_tuning(args.save_tuning)

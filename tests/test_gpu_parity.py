@@ -146,12 +146,19 @@ def test_config1_full_and_depth_recovery(umi):
 
 @pytest.fixture(scope="module")
 def config2(umi):
+    """The full benchmark batch, run in the plans bench.py times (its autotuner)."""
+    import bench
     b = synth.config2()
     W = np.array([umi.window_length(c) for c in b.cadence], np.int32)
     assert np.all(W == 361)
     flux = torch.from_numpy(b.flux).cuda()
-    tr, de = umi.detrend_batched(flux, b.offsets, W)
-    torch.cuda.synchronize()
+    try:
+        umi.clear_tuning()
+        bench.tune_for_batch(umi, b, W)
+        tr, de = umi.detrend_batched(flux, b.offsets, W)
+        torch.cuda.synchronize()
+    finally:
+        umi.clear_tuning()
     return b, W, tr.cpu().numpy(), de.cpu().numpy()
 
 
