@@ -8,7 +8,10 @@
 //      a slot is free; memory is handed out by a first-fit allocator over one
 //      cudaMalloc of the budget;
 //   2. gathers the admitted requests into one batch per idle stream (up to
-//      max_batch_curves), enqueues their host-input copies (device inputs are
+//      max_batch_curves, in arrival order, or with batch_by_window only
+//      requests of the oldest admitted request's window length, so a batch of
+//      short windows never waits for a long band launched before it on the
+//      same stream), enqueues their host-input copies (device inputs are
 //      read in place) and one batched launch
 //      (the persistent work-queue kernel of umi_api.cu) on that stream, then a
 //      completion marker (an event the scheduler polls, or a host callback),
@@ -263,9 +266,24 @@ static void fail_requests_locked(umi_server *s, const std::vector<uint64_t> &tic
 static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mutex> &lk)
 {
     NvtxRange nvtx("umi server batch launch");
-    const size_t take = std::min<size_t>(s->admitted.size(), (size_t)s->cfg.max_batch_curves);
-    std::vector<uint64_t> tickets(s->admitted.begin(), s->admitted.begin() + take);
-    s->admitted.erase(s->admitted.begin(), s->admitted.begin() + take);
+    const size_t cap = (size_t)s->cfg.max_batch_curves;
+    std::vector<uint64_t> tickets;
+    if (s->cfg.batch_by_window) {
+        // The oldest admitted request's window length; the others keep their order.
+        const int32_t W0 = s->reqs[s->admitted.front()]->W;
+        std::vector<uint64_t> rest;
+        rest.reserve(s->admitted.size());
+        for (uint64_t t : s->admitted) {
+            if (tickets.size() < cap && s->reqs[t]->W == W0) tickets.push_back(t);
+            else rest.push_back(t);
+        }
+        s->admitted.swap(rest);
+    } else {
+        const size_t n = std::min(s->admitted.size(), cap);
+        tickets.assign(s->admitted.begin(), s->admitted.begin() + n);
+        s->admitted.erase(s->admitted.begin(), s->admitted.begin() + n);
+    }
+    const size_t take = tickets.size();
     struct Job {
         float *flux, *trend, *detr;
         const float *src_dev;
@@ -432,6 +450,7 @@ void umi_server_default_config(umi_server_config *cfg)
     cfg->device = 0;
     cfg->max_wait_s = 0.0;
     cfg->busy_poll = 1;
+    cfg->batch_by_window = 0;
 }
 
 umi_status umi_server_create(const umi_server_config *cfg_in, umi_server **out)
@@ -443,7 +462,8 @@ umi_status umi_server_create(const umi_server_config *cfg_in, umi_server **out)
     umi_server_default_config(&cfg);
     if (cfg_in) cfg = *cfg_in;
     if (cfg.mem_budget_bytes < 4096 || cfg.max_slots < 1 || cfg.n_streams < 1 || cfg.n_streams > 64 ||
-        cfg.max_batch_curves < 1 || cfg.device < 0 || !(cfg.max_wait_s >= 0.0))
+        cfg.max_batch_curves < 1 || cfg.device < 0 || !(cfg.max_wait_s >= 0.0) ||
+        (cfg.batch_by_window != 0 && cfg.batch_by_window != 1))
         return fail(UMI_ERR_INVALID_ARG, "bad server config");
     cudaError_t e = cudaSetDevice(cfg.device);
     if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");

@@ -133,8 +133,10 @@ def test_errors(umi):
 @pytest.mark.parametrize("busy_poll", [1, 0])
 def test_injected_failures_only_hit_their_requests(umi, busy_poll):
     mix = curves_mix(12)
-    # max_wait_s holds a partial batch back, so the four requests submitted
-    # together form one batch of max_batch_curves = 4.
+    # max_wait_s holds a partial batch back, so the four requests of one
+    # window length submitted together form one batch of max_batch_curves = 4.
+    same = [m for m in mix if m[1] == 361][:4]
+    mix = same + [m for m in mix if m[1] != 361]
     with umi.Server(mem_budget_bytes=1 << 30, n_streams=1, max_batch_curves=4,
                     max_wait_s=2.0, busy_poll=busy_poll) as srv:
         srv.inject_fault(1, 1)                        # the next batch fails to launch
@@ -199,4 +201,23 @@ def test_mixed_scale_modes_and_params_in_one_batch(umi):
             ta, _ = umi.detrend(xd, W, presets[i % len(presets)])
             torch.cuda.synchronize()
             assert np.array_equal(tr, ta.cpu().numpy(), equal_nan=True)
+            srv.release(t)
+
+
+@pytest.mark.parametrize("by_window,expected", [(1, 3), (0, 1)])
+def test_batches_by_window_length(umi, by_window, expected):
+    """Requests held together by max_wait_s: one batch per window length with
+    batch_by_window, one batch in arrival order otherwise (the default);
+    results are the same."""
+    mix = curves_mix(12)
+    with umi.Server(mem_budget_bytes=1 << 30, n_streams=4, max_batch_curves=64,
+                    max_wait_s=0.5, batch_by_window=by_window) as srv:
+        tickets = [srv.submit(x, W) for x, W in mix]
+        for t in tickets:
+            srv.wait(t, 60.0)
+        assert srv.stats()["batches_launched"] == expected
+        for (x, W), t in zip(mix, tickets):
+            tr, _ = srv.copy_out(t, x.size)
+            ta, _ = alone(umi, x, W)
+            assert np.array_equal(tr, ta, equal_nan=True)
             srv.release(t)
