@@ -320,19 +320,41 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
         // ---- exact radix select (chain start / restart) --------------------
         if (__any_sync(0xffffffffu, need_full)) {
             // Bitwise binary search for the key of rank `target` among the S
-            // slots.  It reads the window from shared memory (it runs once per
-            // chain), which keeps the register arrays free for the hot loops.
+            // slots (slots past W and missing samples hold kGap, whose key
+            // sorts below every sample's).  With few slots per lane the keys
+            // are computed once into registers from the window just loaded;
+            // otherwise each pass re-reads the window from shared memory (it
+            // runs once per chain), which keeps the registers free for the
+            // hot loops.
+            constexpr bool kRegKeys = R <= 12;
+            unsigned key[kRegKeys ? R : 1];
             const int wb = q + glane;
             int lim = W - glane;
             asm volatile("" : "+r"(lim));
             unsigned lo = 0xffffffffu, hi = 0u;
+            if constexpr (kRegKeys) {
+#pragma unroll
+                for (int k2 = 0; k2 < R / 2; ++k2) {
+                    key[2 * k2] = float_key(x[k2].x);
+                    key[2 * k2 + 1] = float_key(x[k2].y);
+                    if (x[k2].x > kGapLimit) {
+                        lo = min(lo, key[2 * k2]);
+                        hi = max(hi, key[2 * k2]);
+                    }
+                    if (x[k2].y > kGapLimit) {
+                        lo = min(lo, key[2 * k2 + 1]);
+                        hi = max(hi, key[2 * k2 + 1]);
+                    }
+                }
+            } else {
 #pragma unroll 4
-            for (int i = 0; i < R; ++i) {
-                const float v = tile[wb + G * i];
-                const bool valid = (G * i < lim) && (v > kGapLimit);
-                const unsigned kk = float_key(v);
-                lo = valid ? min(lo, kk) : lo;
-                hi = valid ? max(hi, kk) : hi;
+                for (int i = 0; i < R; ++i) {
+                    const float v = tile[wb + G * i];
+                    const bool valid = (G * i < lim) && (v > kGapLimit);
+                    const unsigned kk = float_key(v);
+                    lo = valid ? min(lo, kk) : lo;
+                    hi = valid ? max(hi, kk) : hi;
+                }
             }
             lo = group_umin<G>(lo);
             hi = group_umax<G>(hi);
@@ -345,10 +367,15 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             for (int b = nb - 1; b >= 0; --b) {
                 const unsigned cand = res | (1u << b);
                 int c = 0;
+                if constexpr (kRegKeys) {
+#pragma unroll
+                    for (int i = 0; i < R; ++i) c += (key[i] < cand) ? 1 : 0;
+                } else {
 #pragma unroll 4
-                for (int i = 0; i < R; ++i) {
-                    const float v = (G * i < lim) ? tile[wb + G * i] : kGap;
-                    c += (float_key(v) < cand) ? 1 : 0;
+                    for (int i = 0; i < R; ++i) {
+                        const float v = (G * i < lim) ? tile[wb + G * i] : kGap;
+                        c += (float_key(v) < cand) ? 1 : 0;
+                    }
                 }
                 c = group_sum_int<G>(c);
                 if (c <= target) res = cand;
