@@ -325,7 +325,12 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             // are computed once into registers from the window just loaded;
             // otherwise each pass re-reads the window from shared memory (it
             // runs once per chain), which keeps the registers free for the
-            // hot loops.
+            // hot loops, and compares floats with the candidate's float:
+            // key order is float order for every non-NaN float except that
+            // -0 sorts below +0, and a candidate whose bits are a NaN is
+            // above (or below) every finite sample, so it compares as +inf
+            // (or -inf).  The -0/+0 case can only change the sign of a zero
+            // median, never its value or the counts that follow.
             constexpr bool kRegKeys = R <= 12;
             unsigned key[kRegKeys ? R : 1];
             const int wb = q + glane;
@@ -371,10 +376,12 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
 #pragma unroll
                     for (int i = 0; i < R; ++i) c += (key[i] < cand) ? 1 : 0;
                 } else {
+                    float candf = key_float(cand);
+                    if (candf != candf) candf = (cand & 0x80000000u) ? INFINITY : -INFINITY;
 #pragma unroll 4
                     for (int i = 0; i < R; ++i) {
                         const float v = (G * i < lim) ? tile[wb + G * i] : kGap;
-                        c += (float_key(v) < cand) ? 1 : 0;
+                        c += (v < candf) ? 1 : 0;
                     }
                 }
                 c = group_sum_int<G>(c);

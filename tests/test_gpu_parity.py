@@ -131,6 +131,26 @@ def test_zero_centred_and_scaled(umi):
     compare_diag(run_diag(umi, x, 61), oracle.detrend(x, 61), scale_aware=True, what="integers", x=x)
 
 
+@pytest.mark.parametrize("W", [25, 61, 361, 2161])
+def test_signed_zeros_and_extreme_magnitudes(umi, W):
+    """Exact selection on windows mixing -0 and +0, both signs and
+    magnitudes from 2^-60 to 2^55: the select's candidates then span the
+    whole order, NaN bit patterns included.  Medians and counts exact."""
+    rng = np.random.default_rng(W)
+    n = 3 * W + 101
+    x = rng.choice(np.array([-0.0, 0.0, -1.0, 1.0, 2.0], np.float32), n)
+    compare_diag(run_diag(umi, x, W), oracle.detrend(x, W), scale_aware=True, what="zeros W=%d" % W, x=x)
+    mag = np.exp2(rng.uniform(-60, 55, n))
+    x = (np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0) * mag).astype(np.float32)
+    x[rng.uniform(size=n) < 0.05] = 0.0
+    got = run_diag(umi, x, W)
+    ref = oracle.detrend(x, W)
+    ok = ~np.isnan(ref["median"])
+    assert np.array_equal(got["median"][ok].astype(np.float64), ref["median"][ok])
+    np.testing.assert_array_equal(got["nvalid"], ref["nvalid"])
+    np.testing.assert_array_equal(got["nplus"], ref["nplus"])
+
+
 def test_config1_full_and_depth_recovery(umi):
     b = synth.config1()
     x = b.curve(0)
