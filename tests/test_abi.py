@@ -112,3 +112,45 @@ def test_header_is_c99_and_host_calls_work(tmp_path, lib):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert "sm_103a" in r.stdout
+
+
+def _cuda_home():
+    return os.environ.get("CUDA_HOME", "/usr/local/cuda")
+
+
+def _build_c_gpu_program(tmp_path):
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    cuda = _cuda_home()
+    exe = tmp_path / "c_abi_gpu"
+    libdir = os.path.dirname(umi.lib_path())
+    cmd = ["gcc", "-std=gnu11", "-O1", "-Wall", "-I", os.path.join(ROOT, "include"),
+           "-I", os.path.join(cuda, "include"),
+           os.path.join(ROOT, "tests", "c_abi_gpu.c"), os.path.join(ROOT, "oracle", "umi_oracle.c"),
+           "-o", str(exe), "-L", libdir, "-lumi", "-L", os.path.join(cuda, "lib64"), "-lcudart",
+           "-lm", "-lpthread", "-Wl,-rpath," + libdir, "-Wl,-rpath," + os.path.join(cuda, "lib64")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_c_gpu_program_builds(tmp_path, lib):
+    """The plain-C GPU client compiles and links against libumi and the CUDA
+    runtime (running it needs a GPU)."""
+    _build_c_gpu_program(tmp_path)
+
+
+@pytest.mark.gpu
+def test_c_gpu_program_runs(tmp_path, lib):
+    """A C99 program drives the batched, host-buffer, single-curve and server
+    entry points through include/umi.h alone, checked against the C oracle."""
+    import subprocess
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    exe = _build_c_gpu_program(tmp_path)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr[-3000:])
+    assert "c gpu ok" in r.stdout
