@@ -106,13 +106,15 @@ static int default_threads(int G) { return G <= 2 ? 128 : 256; }
 
 // Planning constants, measured on GB300 over window lengths 25 to 2161 and
 // bands of 1e4 to 3e6 positions:
-//  * the chain is sized so that about kWarpsPerSm warps per SM get a tile;
+//  * the chain is sized so that about kWarpsPerSm warps per SM get a tile
+//    (kWarpsPerSmNarrow for one- and two-lane groups in the latency regime);
 //  * a band is in the latency regime when, even at the shortest chain of its
 //    throughput variant, it has fewer than kLatencyItemsPerSm tiles per SM;
 //  * below kRegisterRichBelow positions the variant with the larger register
 //    budget wins (the tighter budget pays only once many warps share an SM);
 //  * below kSmallCtaBelow positions 128-thread CTAs spread a band more evenly.
 static const int kWarpsPerSm = 16;
+static const int kWarpsPerSmNarrow = 8;
 static const int kLatencyItemsPerSm = 32;
 static const int64_t kRegisterRichBelow = 500000;
 static const int64_t kSmallCtaBelow = 300000;
@@ -215,11 +217,15 @@ int plan_regime(int W, int64_t positions)
     return items < (int64_t)kLatencyItemsPerSm * sms ? kRegimeLatency : kRegimeThroughput;
 }
 
-// Chain for `positions` windows: about kWarpsPerSm warps per SM get a tile.
-static int chain_for(int G, int64_t positions)
+// Chain for `positions` windows of a band in `regime`: about kWarpsPerSm
+// warps per SM get a tile -- kWarpsPerSmNarrow for groups of one or two lanes
+// in the latency regime, whose chain-start selects (a lane scans its whole
+// window once per bit) cost more than the longer chains they save.
+static int chain_for(int G, int64_t positions, int regime)
 {
     const int sms = std::max(1, device_info(current_device()).sms);
-    const int64_t warps = (int64_t)sms * kWarpsPerSm;
+    const int target = (regime == kRegimeLatency && G <= 2) ? kWarpsPerSmNarrow : kWarpsPerSm;
+    const int64_t warps = (int64_t)sms * target;
     const int64_t per_warp = (positions + warps - 1) / warps;  // windows per warp tile
     return chain_at_least(G, (per_warp * G + 31) / 32);       // 32/G groups share a tile
 }
@@ -255,11 +261,11 @@ umi_status make_plan(int W, int64_t positions, Plan *plan)
     // tuned at a known band size the rule's chain times the ratio the tuner
     // preferred at that size (the tuned chain itself at the tuned size).
     if (positions > 0) {
-        const int rule = std::min(chain_cap(p.G), chain_for(p.G, positions));
+        const int rule = std::min(chain_cap(p.G), chain_for(p.G, positions, regime));
         if (p.tuned_at <= 0) {
             p.chain = std::min(p.chain, rule);
         } else if (positions < p.tuned_at) {
-            const int64_t at = std::min(chain_cap(p.G), chain_for(p.G, p.tuned_at));
+            const int64_t at = std::min(chain_cap(p.G), chain_for(p.G, p.tuned_at, regime));
             p.chain = std::min(p.chain, chain_at_least(p.G, ((int64_t)rule * p.chain + at - 1) / at));
         }
     }
@@ -1255,7 +1261,7 @@ umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *be
         const bool wide = regime == kRegimeLatency && t[v].G == 32 && S >= W && S <= 2 * W;
         if (!tight_fit(t[v], W, smallest) && !wide) continue;
         const int G = t[v].G;
-        const int base = chain_for(G, positions);
+        const int base = chain_for(G, positions, regime);
         std::vector<int> chains;
         for (int64_t target : {(int64_t)8, (int64_t)24, (int64_t)40, (int64_t)72, (int64_t)136,
                                (int64_t)base / 3, (int64_t)base / 2, (int64_t)base, 2 * (int64_t)base,
