@@ -336,6 +336,8 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             const int wb = q + glane;
             int lim = W - glane;
             asm volatile("" : "+r"(lim));
+            // Slot rows of this lane inside the window: G*i < lim.
+            const int rows = lim > 0 ? min(R, (lim + G - 1) / G) : 0;
             unsigned lo = 0xffffffffu, hi = 0u;
             if constexpr (kRegKeys) {
 #pragma unroll
@@ -378,11 +380,10 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                 } else {
                     float candf = key_float(cand);
                     if (candf != candf) candf = (cand & 0x80000000u) ? INFINITY : -INFINITY;
+                    // Rows past W hold kGap: counted once, not read.
 #pragma unroll 4
-                    for (int i = 0; i < R; ++i) {
-                        const float v = (G * i < lim) ? tile[wb + G * i] : kGap;
-                        c += (v < candf) ? 1 : 0;
-                    }
+                    for (int i = 0; i < rows; ++i) c += (tile[wb + G * i] < candf) ? 1 : 0;
+                    c += (kGap < candf) ? R - rows : 0;
                 }
                 c = group_sum_int<G>(c);
                 if (c <= target) res = cand;
