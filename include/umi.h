@@ -133,8 +133,8 @@ umi_status umi_detrend_batched(const float *flux_d, const int64_t *offsets_h, co
 /*
  * umi_detrend_batched on HOST buffers: copies flux_h to the device, runs the
  * batched path and copies trend_h / detr_h back, and waits for all of it
- * before returning.  Batches of more than a few million samples are split
- * into up to 8 chunks of whole curves, pipelined over `stream`, a second
+ * before returning.  Batches of more than a couple of million samples are
+ * split into up to 16 chunks of whole curves, pipelined over `stream`, a second
  * compute stream and two copy streams so that copies overlap the detrend;
  * every chunk is planned from the whole batch's bands, so the result does not
  * depend on the chunking.  The three side streams and the pipeline's events

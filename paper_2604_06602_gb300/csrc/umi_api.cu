@@ -1109,8 +1109,8 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
     // Pipeline over chunks of curves: the copy-in of chunk c+1 and the
     // copy-out of chunk c-1 overlap the detrend of chunk c (copy engines and
     // SMs work at once; pinned host buffers make the copies asynchronous).
-    const int64_t kChunkSamples = 2 << 20;
-    const int K = (int)std::max<int64_t>(1, std::min<int64_t>({8, B, total / kChunkSamples}));
+    const int64_t kChunkSamples = 1 << 20;
+    const int K = (int)std::max<int64_t>(1, std::min<int64_t>({16, B, total / kChunkSamples}));
     std::vector<int32_t> cut(1, 0);
     for (int c = 1; c < K; ++c) {
         const int64_t target = total * c / K;
