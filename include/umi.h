@@ -294,8 +294,8 @@ void umi_set_graph_cache(int enabled);
  * budget.  A scheduler thread admits queued requests while their resident
  * bytes (trend + detr, plus a copy of the flux for host inputs: 8 or 12 bytes
  * per sample, plus alignment) fit the budget and a slot is free, gathers the
- * admitted requests into batched launches (in arrival order, or one window
- * length per batch) on `n_streams` streams so that batches overlap on the GPU, and
+ * admitted requests into batched launches (one window length per batch, or
+ * arrival order) on `n_streams` streams so that batches overlap on the GPU, and
  * marks each request done when its batch's completion event fires.  Results
  * stay on the device until released.
  * ------------------------------------------------------------------------ */
@@ -314,13 +314,12 @@ typedef struct {
                                   cudaEventQuery (lowest latency, one host core
                                   busy); 0: it sleeps on a condition variable and
                                   learns of finished batches from host callbacks */
-    int32_t batch_by_window;   /* 0 (default): batches take admitted requests in
-                                  arrival order whatever their window length;
-                                  1: a batch holds requests of one window length
-                                  (the oldest admitted request's), so short windows
-                                  never wait for a long band of the same batch
-                                  (lower p50 under load, higher p99 for the long
-                                  class, which waits its turn) */
+    int32_t batch_by_window;   /* 1 (default): a batch holds requests of one window
+                                  length (the oldest admitted request's), so short
+                                  windows never wait for a long band of the same
+                                  batch and the window classes run on separate
+                                  streams; 0: batches take admitted requests in
+                                  arrival order whatever their window length */
 } umi_server_config;
 
 typedef struct {

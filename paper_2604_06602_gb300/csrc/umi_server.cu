@@ -8,10 +8,10 @@
 //      a slot is free; memory is handed out by a first-fit allocator over one
 //      cudaMalloc of the budget;
 //   2. gathers the admitted requests into one batch per idle stream (up to
-//      max_batch_curves, in arrival order, or with batch_by_window only
-//      requests of the oldest admitted request's window length, so a batch of
-//      short windows never waits for a long band launched before it on the
-//      same stream), enqueues their host-input copies (device inputs are
+//      max_batch_curves; by default only requests of the oldest admitted
+//      request's window length, so a batch of short windows never waits for
+//      a long band launched before it on the same stream; or in arrival
+//      order), enqueues their host-input copies (device inputs are
 //      read in place) and one batched launch
 //      (the persistent work-queue kernel of umi_api.cu) on that stream, then a
 //      completion marker (an event the scheduler polls, or a host callback),
@@ -450,7 +450,7 @@ void umi_server_default_config(umi_server_config *cfg)
     cfg->device = 0;
     cfg->max_wait_s = 0.0;
     cfg->busy_poll = 1;
-    cfg->batch_by_window = 0;
+    cfg->batch_by_window = 1;
 }
 
 umi_status umi_server_create(const umi_server_config *cfg_in, umi_server **out)

@@ -207,7 +207,7 @@ def test_mixed_scale_modes_and_params_in_one_batch(umi):
 @pytest.mark.parametrize("by_window,expected", [(1, 3), (0, 1)])
 def test_batches_by_window_length(umi, by_window, expected):
     """Requests held together by max_wait_s: one batch per window length with
-    batch_by_window, one batch in arrival order otherwise (the default);
+    batch_by_window (the default), one batch in arrival order otherwise;
     results are the same."""
     mix = curves_mix(12)
     with umi.Server(mem_budget_bytes=1 << 30, n_streams=4, max_batch_curves=64,
