@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "umi_host.h"
 #include "umi_internal.h"
 
 namespace umi {
@@ -39,78 +40,6 @@ __global__ void validity_bits_kernel(const float *__restrict__ flux, int64_t tot
     }
 }
 
-namespace {
-
-// Reader over the 32-bit-word validity mask: word-at-a-time run scans.
-struct Bits {
-    const unsigned *w;
-    // First index in [i, end) whose bit equals `want`, or end.
-    int64_t find(int64_t i, int64_t end, bool want) const
-    {
-        while (i < end) {
-            unsigned word = w[i >> 5];
-            if (!want) word = ~word;
-            word &= ~0u << (i & 31);  // ignore bits below i
-            if (word) {
-                const int64_t j = (i & ~(int64_t)31) + __builtin_ctz(word);
-                return j < end ? j : end;
-            }
-            i = (i & ~(int64_t)31) + 32;
-        }
-        return end;
-    }
-    // Valid samples in [a, b).
-    int64_t count(int64_t a, int64_t b) const
-    {
-        int64_t c = 0;
-        while (a < b) {
-            const int64_t word_end = std::min<int64_t>((a & ~(int64_t)31) + 32, b);
-            unsigned word = w[a >> 5] >> (a & 31);
-            const int nb = (int)(word_end - a);
-            if (nb < 32) word &= (1u << nb) - 1u;
-            c += __builtin_popcount(word);
-            a = word_end;
-        }
-        return c;
-    }
-};
-
-struct Segment {
-    int64_t start, len;
-};
-
-// Kept segments of the curve occupying [o, o + n) of the flat array.
-void find_segments(const Bits &bits, int64_t o, int64_t n, int64_t gap_min, int64_t min_seg,
-                   std::vector<Segment> *out)
-{
-    const int64_t end = o + n;
-    int64_t j = bits.find(o, end, true);  // first valid sample
-    while (j < end) {
-        const int64_t start = j;
-        int64_t cur = j;  // last valid sample known to be in this segment
-        int64_t last, next;
-        for (;;) {
-            const int64_t g = bits.find(cur + 1, end, false);  // next missing sample
-            if (g >= end) {                                      // valid up to the end
-                last = end - 1;
-                next = end;
-                break;
-            }
-            const int64_t v = bits.find(g, end, true);  // first valid after the run
-            if (v >= end || v - g >= gap_min) {          // trailing run, or a split
-                last = g - 1;
-                next = v;
-                break;
-            }
-            cur = v;  // a short run of missing samples stays inside the segment
-        }
-        const int64_t valid = bits.count(start, last + 1);
-        if (valid >= 1 && valid >= min_seg) out->push_back(Segment{start - o, last + 1 - start});
-        j = next;
-    }
-}
-
-}  // namespace
 
 umi_status detrend_segmented(const float *flux, const int64_t *offsets, const int32_t *W, int32_t B,
                              const umi_params *params, const umi_segment_params *seg, float *trend,

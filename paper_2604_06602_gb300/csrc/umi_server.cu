@@ -36,6 +36,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "umi_host.h"
 #include "umi_internal.h"
 
 namespace umi {
@@ -45,50 +46,6 @@ static double now_s()
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// First-fit allocator over [0, capacity) with coalescing of free ranges.
-class ArenaAllocator {
-  public:
-    explicit ArenaAllocator(size_t capacity) : cap_(capacity) { free_[0] = capacity; }
-    bool alloc(size_t bytes, size_t *off)
-    {
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                const size_t rest = it->second - bytes;
-                const size_t start = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[start] = rest;
-                used_ += bytes;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes)
-    {
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-        used_ -= bytes;
-    }
-    size_t used() const { return used_; }
-    size_t capacity() const { return cap_; }
-
-  private:
-    size_t cap_;
-    size_t used_ = 0;
-    std::map<size_t, size_t> free_;  // offset -> length
-};
 
 enum class ReqState { Queued, Admitted, Running, Done, Failed };
 

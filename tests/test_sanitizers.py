@@ -1,7 +1,8 @@
-"""Host-side memory and undefined-behaviour checks: the C oracle built with
-AddressSanitizer and UndefinedBehaviorSanitizer, driven over its edge cases
-(compute-sanitizer is not available for the GPU side; the kernels' own
-checked build covers that, see test_checked_build.py)."""
+"""Host-side memory and undefined-behaviour checks, with AddressSanitizer and
+UndefinedBehaviorSanitizer: the C oracle driven over its edge cases, and the
+library's host-only pieces against brute-force models (compute-sanitizer is
+not available for the GPU side; the kernels' own checked build covers that,
+see test_checked_build.py)."""
 import os
 import shutil
 import subprocess
@@ -31,3 +32,25 @@ def test_oracle_under_asan_and_ubsan(tmp_path):
     assert r.returncode == 0, (r.stdout, r.stderr[-4000:])
     assert "runtime error" not in r.stderr and "AddressSanitizer" not in r.stderr
     assert "0 failures" in r.stdout
+
+
+def test_host_pieces_under_asan_and_ubsan(tmp_path):
+    """The library's host-only pieces (the server's arena allocator and the
+    segmented entry point's gap scan, csrc/umi_host.h) built with the
+    sanitizers and checked against brute-force models."""
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("g++ not available")
+    exe = tmp_path / "host_sanitize"
+    cmd = [cxx, "-std=c++17", "-O1", "-g", "-fno-omit-frame-pointer",
+           "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined",
+           "-I", os.path.join(ROOT, "paper_2604_06602_gb300", "csrc"),
+           os.path.join(ROOT, "tests", "host_sanitize_driver.cpp"), "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0 and "sanitize" in r.stderr and "cannot find" in r.stderr:
+        pytest.skip("sanitizer runtime not installed")
+    assert r.returncode == 0, r.stderr
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=1", UBSAN_OPTIONS="print_stacktrace=1:halt_on_error=1")
+    r = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, (r.stdout, r.stderr[-4000:])
+    assert "host ok" in r.stdout
