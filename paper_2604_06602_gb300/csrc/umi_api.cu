@@ -381,32 +381,24 @@ static Curve make_curve(const float *flux, float *trend, float *detr, int64_t n,
 }
 
 // -------------------------------------------------------- single curve --
-static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const umi_params *params,
-                                 float *trend, float *detr, const Diag *diag, cudaStream_t stream)
+umi_status launch_single_curve(const Curve &c, int64_t plan_positions, const Diag *diag,
+                               cudaStream_t stream, int *launches)
 {
-    NvtxRange nvtx("umi detrend");
-    clear_error();
-    umi_params p;
-    umi_status st = check_params(params, &p);
-    if (st != UMI_OK) return st;
-    if (n < 0) return fail(UMI_ERR_INVALID_ARG, "n must be >= 0");
-    if (W < 1 || (W % 2) == 0 || W > kMaxWindow)
-        return fail(UMI_ERR_INVALID_ARG, "W must be odd and in [1, " + std::to_string(kMaxWindow) + "]");
-    if (n == 0) return UMI_OK;
-    if (!flux || !trend || !detr) return fail(UMI_ERR_INVALID_ARG, "null buffer");
+    if (launches) *launches = 0;
+    if (c.n <= 0) return UMI_OK;
     Plan plan;
-    st = make_plan(W, n, &plan);
+    umi_status st = make_plan(c.W, plan_positions, &plan);
     if (st != UMI_OK) return st;
-    const int flavour = (diag ? kFlagDiag : 0) | (p.scale_mode == UMI_SCALE_MAD ? kFlagMad : 0);
+    const int flavour = (diag ? kFlagDiag : 0) | (c.scale_mode == UMI_SCALE_MAD ? kFlagMad : 0);
     st = prepare_kernel(plan, flavour);
     if (st != UMI_OK) return st;
     const int64_t T = plan.tile();
-    const int64_t items = (n + T - 1) / T;
+    const int64_t items = (c.n + T - 1) / T;
     if (items > INT32_MAX) return fail(UMI_ERR_INVALID_ARG, "curve too long");
     LaunchArgs a;
     memset(&a, 0, sizeof(a));
     a.curves = nullptr;
-    a.single = make_curve(flux, trend, detr, n, W, p);
+    a.single = c;
     a.items = nullptr;
     a.n_items = (int32_t)items;
     a.chain = plan.chain;
@@ -421,7 +413,24 @@ static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const 
     const int64_t grid = (items + warps - 1) / warps;
     cudaError_t e = fn(a, (int)grid, plan.threads, plan.smem_bytes(), stream);
     if (e != cudaSuccess) return fail_cuda(e, "kernel launch");
+    if (launches) *launches = 1;
     return UMI_OK;
+}
+
+static umi_status detrend_single(const float *flux, int64_t n, int32_t W, const umi_params *params,
+                                 float *trend, float *detr, const Diag *diag, cudaStream_t stream)
+{
+    NvtxRange nvtx("umi detrend");
+    clear_error();
+    umi_params p;
+    umi_status st = check_params(params, &p);
+    if (st != UMI_OK) return st;
+    if (n < 0) return fail(UMI_ERR_INVALID_ARG, "n must be >= 0");
+    if (W < 1 || (W % 2) == 0 || W > kMaxWindow)
+        return fail(UMI_ERR_INVALID_ARG, "W must be odd and in [1, " + std::to_string(kMaxWindow) + "]");
+    if (n == 0) return UMI_OK;
+    if (!flux || !trend || !detr) return fail(UMI_ERR_INVALID_ARG, "null buffer");
+    return launch_single_curve(make_curve(flux, trend, detr, n, W, p), n, diag, stream, nullptr);
 }
 
 // ------------------------------------------------------------- batches --
@@ -664,6 +673,16 @@ umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t str
 {
     if (launches) *launches = 0;
     if (curves.empty()) return UMI_OK;
+    if (curves.size() == 1) {
+        // One curve needs no work-queue tables: nothing is copied to the
+        // device before the kernel.  The plan is the one-curve band's.
+        int64_t P = curves[0].n;
+        if (plan_sizes) {
+            auto it = plan_sizes->find(std::make_pair(curves[0].W, curves[0].scale_mode));
+            if (it != plan_sizes->end()) P = std::max(P, it->second);
+        }
+        return launch_single_curve(curves[0], P, nullptr, stream, launches);
+    }
     BatchLayout lay;
     umi_status st = build_layout(curves, &lay, plan_sizes);
     if (st != UMI_OK) return st;

@@ -78,6 +78,12 @@ using BandSizes = std::map<std::pair<int, int>, int64_t>;
 umi_status launch_curve_table(const std::vector<Curve> &curves, cudaStream_t stream,
                               int *launches, const BandSizes *plan_sizes = nullptr);
 
+// One curve in one launch without work-queue tables (the kernel numbers the
+// curve's tiles itself): nothing is copied to the device first.
+// `plan_positions` is the size of the band the curve is planned with.
+umi_status launch_single_curve(const Curve &c, int64_t plan_positions, const Diag *diag,
+                               cudaStream_t stream, int *launches);
+
 // Adds to the process-wide count of kernels launched by libumi.
 void count_launches(int n);
 

@@ -295,32 +295,39 @@ static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mute
         curves.push_back(c);
     }
     int launches = 0;
-    PreparedBatch pb;
-    if (ok && prepare_batch(curves, &pb) != UMI_OK) ok = false;
-    StreamBuffers &sb = s->bufs[k];
-    // This stream's previous batch has completed (it is idle), so its buffers
-    // may be regrown or rewritten.
-    if (ok && pb.dev_bytes > sb.dev_bytes) {
-        if (sb.dev) cudaFree(sb.dev);
-        sb.dev = nullptr;
-        sb.dev_bytes = 0;
-        if (cudaMalloc((void **)&sb.dev, 2 * pb.dev_bytes) == cudaSuccess) sb.dev_bytes = 2 * pb.dev_bytes;
-        else ok = false;
+    if (curves.size() == 1) {
+        // A batch of one request needs no work-queue tables (the common case
+        // at low load): its kernel follows the input copy directly.
+        if (ok && launch_single_curve(curves[0], curves[0].n, nullptr, st, &launches) != UMI_OK) ok = false;
+    } else {
+        PreparedBatch pb;
+        if (ok && prepare_batch(curves, &pb) != UMI_OK) ok = false;
+        StreamBuffers &sb = s->bufs[k];
+        // This stream's previous batch has completed (it is idle), so its
+        // buffers may be regrown or rewritten.
+        if (ok && pb.dev_bytes > sb.dev_bytes) {
+            if (sb.dev) cudaFree(sb.dev);
+            sb.dev = nullptr;
+            sb.dev_bytes = 0;
+            if (cudaMalloc((void **)&sb.dev, 2 * pb.dev_bytes) == cudaSuccess) sb.dev_bytes = 2 * pb.dev_bytes;
+            else ok = false;
+        }
+        if (ok && pb.host_bytes > sb.host_bytes) {
+            if (sb.host) cudaFreeHost(sb.host);
+            sb.host = nullptr;
+            sb.host_bytes = 0;
+            if (cudaMallocHost((void **)&sb.host, 2 * pb.host_bytes) == cudaSuccess) sb.host_bytes = 2 * pb.host_bytes;
+            else ok = false;
+        }
+        if (ok && enqueue_prepared(curves, pb, sb.dev, sb.host, st, &launches) != UMI_OK) ok = false;
     }
-    if (ok && pb.host_bytes > sb.host_bytes) {
-        if (sb.host) cudaFreeHost(sb.host);
-        sb.host = nullptr;
-        sb.host_bytes = 0;
-        if (cudaMallocHost((void **)&sb.host, 2 * pb.host_bytes) == cudaSuccess) sb.host_bytes = 2 * pb.host_bytes;
-        else ok = false;
-    }
-    if (ok && enqueue_prepared(curves, pb, sb.dev, sb.host, st, &launches) != UMI_OK) ok = false;
     if (ok) {
         const cudaError_t e = s->cfg.busy_poll ? cudaEventRecord(s->done_events[k], st)
                                                : cudaLaunchHostFunc(st, batch_done_cb, batch.get());
         if (e != cudaSuccess) ok = false;
     }
     const double t_enq = now_s() - t_enq0;
+    count_launches(launches);
 
     lk.lock();
     s->stats.launch_host_s += t_enq;

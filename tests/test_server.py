@@ -73,8 +73,10 @@ def test_device_inputs_and_poll_pointers(umi):
     x = synth.random_curve(3, 4000)
     xd = torch.from_numpy(x).cuda()
     with umi.Server(mem_budget_bytes=64 << 20) as srv:
+        launches0 = umi.kernel_launch_count()
         t = srv.submit(xd, 361)
         srv.wait(t, 60.0)
+        assert umi.kernel_launch_count() > launches0     # server kernels are counted too
         tr_ptr, de_ptr, lat = srv.poll(t)
         assert tr_ptr and de_ptr and lat > 0
         tl = srv.timeline(t)
