@@ -509,3 +509,27 @@ def test_split_long_curve_matches_whole(umi, n, W, parts):
             compare_trend(t, t0[a:b].astype(np.float64), what="part %d" % a)
             compare_detr(d, d0[a:b].astype(np.float64), what="part %d" % a)
     assert kinds == ({"same"} if W == 2161 else {"differ"})
+
+
+@pytest.mark.parametrize("W", [7, 25, 61, 129, 361, 721, 2161])
+def test_random_parameters(umi, W):
+    """Seeded random estimator parameters (alpha on both sides of 1, c, the
+    iteration count, min_valid, both scale modes) on gappy curves, against
+    the oracle."""
+    rng = np.random.default_rng(4000 + W)
+    for trial in range(3):
+        alpha = float(np.exp(rng.uniform(np.log(0.3), np.log(12.0))))
+        c = float(rng.uniform(1.5, 8.0))
+        iters = int(rng.integers(0, 10))
+        min_valid = int(rng.choice([-1, 0, W // 2, W]))
+        mad = bool(trial == 2)
+        n = int(rng.integers(2 * W + 50, 4 * W + 500))
+        x = synth.random_curve(5000 + 10 * W + trial, n, nan_frac=0.03, nan_runs=2, run_len=(1, W),
+                               ties=bool(trial == 1))
+        p = umi.params(alpha=alpha, c=c, iters=iters, min_valid=min_valid,
+                       scale_mode=umi.SCALE_MAD if mad else umi.SCALE_UPPER_RMS)
+        ref = oracle.detrend(x, W, alpha=alpha, c=c, iters=iters, min_valid=min_valid,
+                             scale_mode=oracle.SCALE_MAD if mad else oracle.SCALE_UPPER_RMS)
+        compare_diag(run_diag(umi, x, W, p), ref, c=c,
+                     what="W=%d alpha=%.3g c=%.3g iters=%d min_valid=%d mad=%d"
+                     % (W, alpha, c, iters, min_valid, mad))
