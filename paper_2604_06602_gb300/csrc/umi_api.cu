@@ -766,13 +766,17 @@ static umi_status build_graph(const std::vector<Curve> &curves, GraphEntry *g)
         st = prepare_kernel(band.plan, band.flavour);
         if (st != UMI_OK) return st;
     }
+    // One curve needs no tables: the graph holds its kernel alone.
+    const bool one = curves.size() == 1;
     const Scratch sc = scratch_layout(curves.size(), lay.items.size(), lay.bands.size());
-    std::vector<char> host(sc.counter_off);
-    memcpy(host.data() + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
-    if (!lay.items.empty())
-        memcpy(host.data() + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
-    UMI_CUDA(cudaMalloc(&g->dev, sc.bytes), "cudaMalloc (graph tables)");
-    UMI_CUDA(cudaMemcpy(g->dev, host.data(), sc.counter_off, cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (!one) {
+        std::vector<char> host(sc.counter_off);
+        memcpy(host.data() + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
+        if (!lay.items.empty())
+            memcpy(host.data() + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
+        UMI_CUDA(cudaMalloc(&g->dev, sc.bytes), "cudaMalloc (graph tables)");
+        UMI_CUDA(cudaMemcpy(g->dev, host.data(), sc.counter_off, cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
     cudaStream_t cs;
     UMI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
     cudaGraph_t graph = nullptr;
@@ -781,7 +785,8 @@ static umi_status build_graph(const std::vector<Curve> &curves, GraphEntry *g)
         cudaStreamDestroy(cs);
         return fail_cuda(e, "cudaStreamBeginCapture");
     }
-    umi_status est = enqueue_bands(lay, (char *)g->dev, sc, cs, &g->launches);
+    umi_status est = one ? launch_single_curve(curves[0], curves[0].n, nullptr, cs, &g->launches)
+                         : enqueue_bands(lay, (char *)g->dev, sc, cs, &g->launches);
     e = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
     if (est != UMI_OK) {
