@@ -617,7 +617,19 @@ def serving_leg(umi, torch, dev, args):
                                      "gpu": float(np.median(ph[:, 2] - ph[:, 1]) * 1e3)}})
         out["mean_batch_curves"] = st["mean_batch_curves"]
         out["batches"] = st["batches_launched"]
-    out["policy"] = "one window length per batch (batch_by_window = 1, the default)"
+    out["policy"] = ("one window length per batch, windows >= 1025 on low-priority streams "
+                     "(the defaults: batch_by_window = 1, priority_window = 1025)")
+    # The same stream without stream priorities.
+    out["no_priority_rates"] = []
+    with umi.Server(mem_budget_bytes=40 << 30, n_streams=4, max_batch_curves=512,
+                    priority_window=0) as srv:
+        for rate in (10000.0, 20000.0):
+            n = int(min(n_max, max(1000, rate * 0.6)))
+            lat, wall, offered, ph = serve_at_rate(umi, srv, dev_pool, Ws, which, arrivals / rate, n)
+            out["no_priority_rates"].append({"rate_hz": rate, "offered_hz": offered, "requests": n,
+                                          "curves_per_s": n / wall,
+                                          "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                                          "p99_ms": float(np.percentile(lat, 99) * 1e3)})
     # The same stream under the other batching policy: arrival order.
     out["arrival_order_rates"] = []
     with umi.Server(mem_budget_bytes=40 << 30, n_streams=4, max_batch_curves=512,

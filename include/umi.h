@@ -320,6 +320,13 @@ typedef struct {
                                   batch and the window classes run on separate
                                   streams; 0: batches take admitted requests in
                                   arrival order whatever their window length */
+    int32_t priority_window;   /* with batch_by_window and n_streams >= 2:
+                                  batches of windows at least this long run on
+                                  the low-priority half of the streams and shorter
+                                  ones on the high-priority half, so short windows
+                                  pass queued long ones on the GPU (default 1025,
+                                  which separates 20-s-cadence windows; 0: all
+                                  streams have the same priority) */
 } umi_server_config;
 
 typedef struct {

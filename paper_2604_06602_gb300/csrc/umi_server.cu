@@ -220,14 +220,13 @@ static void fail_requests_locked(umi_server *s, const std::vector<uint64_t> &tic
 
 // Launches one batch on stream k; called with the lock held, drops it while
 // enqueuing device work.
-static void launch_batch_locked(umi_server *s, int k, std::unique_lock<std::mutex> &lk)
+static void launch_batch_locked(umi_server *s, int k, int32_t W0, std::unique_lock<std::mutex> &lk)
 {
     NvtxRange nvtx("umi server batch launch");
     const size_t cap = (size_t)s->cfg.max_batch_curves;
     std::vector<uint64_t> tickets;
     if (s->cfg.batch_by_window) {
-        // The oldest admitted request's window length; the others keep their order.
-        const int32_t W0 = s->reqs[s->admitted.front()]->W;
+        // Requests of window length W0, in arrival order; the others keep theirs.
         std::vector<uint64_t> rest;
         rest.reserve(s->admitted.size());
         for (uint64_t t : s->admitted) {
@@ -367,11 +366,41 @@ static void scheduler_main(umi_server *s)
             }
         }
         bool launched = false;
-        for (size_t k = 0; !hold && k < s->streams.size() && !s->admitted.empty(); ++k) {
-            if (s->inflight[k]) continue;
-            launch_batch_locked(s, (int)k, lk);
+        while (!hold && !s->admitted.empty() && !s->stop) {
+            // The window length to batch (the oldest admitted request's) and
+            // an idle stream for it.  With priority_window, long windows
+            // take only the low-priority half of the streams; when none of
+            // those is idle, the oldest short-window request goes first
+            // (short windows prefer the high-priority half).
+            const int n = (int)s->streams.size();
+            const int pw = s->cfg.priority_window;
+            auto idle = [&](int a, int b) {
+                for (int k = a; k < b; ++k)
+                    if (!s->inflight[k]) return k;
+                return -1;
+            };
+            int32_t W0 = s->reqs[s->admitted.front()]->W;
+            int k = -1;
+            if (pw <= 0) {
+                k = idle(0, n);
+            } else if (W0 >= pw) {
+                k = idle(n / 2, n);
+                if (k < 0) {
+                    W0 = -1;
+                    for (uint64_t t : s->admitted)
+                        if (s->reqs[t]->W < pw) {
+                            W0 = s->reqs[t]->W;
+                            break;
+                        }
+                }
+            }
+            if (pw > 0 && W0 >= 0 && W0 < pw) {
+                k = idle(0, n / 2);
+                if (k < 0) k = idle(n / 2, n);
+            }
+            if (k < 0 || W0 < 0) break;
+            launch_batch_locked(s, k, W0, lk);
             launched = true;
-            if (s->stop) break;
         }
         if (launched) continue;
         if (s->cfg.busy_poll) {
@@ -415,6 +444,7 @@ void umi_server_default_config(umi_server_config *cfg)
     cfg->max_wait_s = 0.0;
     cfg->busy_poll = 1;
     cfg->batch_by_window = 1;
+    cfg->priority_window = 1025;
 }
 
 umi_status umi_server_create(const umi_server_config *cfg_in, umi_server **out)
@@ -427,8 +457,10 @@ umi_status umi_server_create(const umi_server_config *cfg_in, umi_server **out)
     if (cfg_in) cfg = *cfg_in;
     if (cfg.mem_budget_bytes < 4096 || cfg.max_slots < 1 || cfg.n_streams < 1 || cfg.n_streams > 64 ||
         cfg.max_batch_curves < 1 || cfg.device < 0 || !(cfg.max_wait_s >= 0.0) ||
-        (cfg.batch_by_window != 0 && cfg.batch_by_window != 1))
+        (cfg.batch_by_window != 0 && cfg.batch_by_window != 1) || cfg.priority_window < 0)
         return fail(UMI_ERR_INVALID_ARG, "bad server config");
+    // Priorities need window-homogeneous batches and streams to split.
+    if (!cfg.batch_by_window || cfg.n_streams < 2) cfg.priority_window = 0;
     cudaError_t e = cudaSetDevice(cfg.device);
     if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
     std::unique_ptr<umi_server> s(new umi_server());
@@ -440,8 +472,16 @@ umi_status umi_server_create(const umi_server_config *cfg_in, umi_server **out)
     s->done_events.resize(cfg.n_streams);
     s->bufs.resize(cfg.n_streams);
     s->inflight.resize(cfg.n_streams);
+    int least = 0, greatest = 0;
+    if (cfg.priority_window > 0 && cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
     for (int k = 0; k < cfg.n_streams; ++k) {
-        e = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
+        // With priority_window, streams [0, n/2) take short windows at the
+        // greatest priority and the rest long windows at the least.
+        const int prio = cfg.priority_window > 0 ? (k < cfg.n_streams / 2 ? greatest : least) : 0;
+        e = cudaStreamCreateWithPriority(&s->streams[k], cudaStreamNonBlocking, prio);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->done_events[k], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             for (auto &x : s->streams)

@@ -76,7 +76,8 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("max_batch_curves", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("max_wait_s", ctypes.c_double),
-                ("busy_poll", ctypes.c_int32), ("batch_by_window", ctypes.c_int32)]
+                ("busy_poll", ctypes.c_int32), ("batch_by_window", ctypes.c_int32),
+                ("priority_window", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -382,7 +383,8 @@ class Server:
     """Continuous-batching server (umi_server_*)."""
 
     def __init__(self, mem_budget_bytes=None, max_slots=None, n_streams=None, max_batch_curves=None,
-                 device=0, max_wait_s=None, busy_poll=None, batch_by_window=None):
+                 device=0, max_wait_s=None, busy_poll=None, batch_by_window=None,
+                 priority_window=None):
         cfg = ServerConfig()
         load().umi_server_default_config(ctypes.byref(cfg))
         if mem_budget_bytes is not None:
@@ -399,6 +401,8 @@ class Server:
             cfg.busy_poll = int(busy_poll)
         if batch_by_window is not None:
             cfg.batch_by_window = int(batch_by_window)
+        if priority_window is not None:
+            cfg.priority_window = int(priority_window)
         cfg.device = int(device)
         h = ctypes.c_void_p()
         _check(load().umi_server_create(ctypes.byref(cfg), ctypes.byref(h)))

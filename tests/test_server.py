@@ -223,3 +223,33 @@ def test_batches_by_window_length(umi, by_window, expected):
             ta, _ = alone(umi, x, W)
             assert np.array_equal(tr, ta, equal_nan=True)
             srv.release(t)
+
+
+@pytest.mark.parametrize("priority_window", [0, 1025, 26])
+def test_stream_priorities(umi, priority_window):
+    """Long windows on the low-priority half of the streams (the default
+    threshold 1025, a threshold that sends W = 361 there too, and none):
+    every result equals the curve alone, and no class starves."""
+    mix = curves_mix(30)
+    with umi.Server(mem_budget_bytes=1 << 30, n_streams=4, max_batch_curves=4,
+                    priority_window=priority_window) as srv:
+        tickets = [srv.submit(x, W) for x, W in mix]
+        for t in tickets:
+            srv.wait(t, 120.0)
+        for (x, W), t in zip(mix, tickets):
+            tr, _ = srv.copy_out(t, x.size)
+            ta, _ = alone(umi, x, W)
+            assert np.array_equal(tr, ta, equal_nan=True)
+            srv.release(t)
+        assert srv.stats()["completed"] == len(mix)
+
+
+def test_priority_config_checks(umi):
+    with pytest.raises(umi.UmiError):
+        umi.Server(mem_budget_bytes=1 << 20, priority_window=-1)
+    # Priorities need window-homogeneous batches and two streams; otherwise they are off.
+    with umi.Server(mem_budget_bytes=1 << 20, n_streams=1) as srv:
+        x = synth.random_curve(5, 500)
+        t = srv.submit(x, 25)
+        srv.wait(t, 60.0)
+        srv.release(t)
