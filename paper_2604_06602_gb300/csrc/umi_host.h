@@ -3,7 +3,9 @@
 // AddressSanitizer and UndefinedBehaviorSanitizer):
 //   * the server's first-fit arena allocator (umi_server.cu);
 //   * the gap scan of the segmented entry point (umi_segments.cu), which
-//     reads a 1-bit-per-sample validity mask.
+//     reads a 1-bit-per-sample validity mask;
+//   * the server's batching policy: which window length and stream the next
+//     batch takes, and which admitted requests go into it.
 #pragma once
 
 #include <algorithm>
@@ -126,6 +128,81 @@ inline void find_segments(const Bits &bits, int64_t o, int64_t n, int64_t gap_mi
         const int64_t valid = bits.count(start, last + 1);
         if (valid >= 1 && valid >= min_seg) out->push_back(Segment{start - o, last + 1 - start});
         j = next;
+    }
+}
+
+// ---- serving policy ---------------------------------------------------------
+// The admitted queue holds tickets in arrival order; window(t) is a ticket's
+// window length W and idle(k) tells whether stream k has no batch in flight.
+
+struct BatchChoice {
+    int stream = -1;  // -1: nothing is launched now
+    int32_t W = -1;   // the window length the batch takes
+};
+
+// The oldest admitted request names the window length, and any idle stream
+// takes it.  With priority_window > 0 the streams split in halves: windows
+// with W >= priority_window run only on the low-priority half [n/2, n); when
+// none of those is idle, the oldest request with a shorter window goes
+// instead.  Short windows take the high-priority half [0, n/2) first and the
+// other half when all of it is busy.
+template <class WindowOf, class IdleFn>
+inline BatchChoice choose_batch(const std::vector<uint64_t> &admitted, WindowOf window, IdleFn idle,
+                                int n_streams, int priority_window)
+{
+    BatchChoice c;
+    if (admitted.empty()) return c;
+    auto first_idle = [&](int a, int b) {
+        for (int k = a; k < b; ++k)
+            if (idle(k)) return k;
+        return -1;
+    };
+    const int pw = priority_window;
+    int32_t W0 = window(admitted.front());
+    int k = -1;
+    if (pw <= 0) {
+        k = first_idle(0, n_streams);
+    } else if (W0 >= pw) {
+        k = first_idle(n_streams / 2, n_streams);
+        if (k < 0) {
+            W0 = -1;
+            for (uint64_t t : admitted)
+                if (window(t) < pw) {
+                    W0 = window(t);
+                    break;
+                }
+        }
+    }
+    if (pw > 0 && W0 >= 0 && W0 < pw) {
+        k = first_idle(0, n_streams / 2);
+        if (k < 0) k = first_idle(n_streams / 2, n_streams);
+    }
+    if (k < 0 || W0 < 0) return c;
+    c.stream = k;
+    c.W = W0;
+    return c;
+}
+
+// Moves the next batch out of `admitted` into `tickets`.  By window: up to
+// `cap` requests of window length W, in arrival order, while the others keep
+// theirs.  Otherwise the first `cap` requests, whatever their windows.
+template <class WindowOf>
+inline void take_batch(std::vector<uint64_t> *admitted, WindowOf window, int32_t W, size_t cap, bool by_window,
+                       std::vector<uint64_t> *tickets)
+{
+    tickets->clear();
+    if (by_window) {
+        std::vector<uint64_t> rest;
+        rest.reserve(admitted->size());
+        for (uint64_t t : *admitted) {
+            if (tickets->size() < cap && window(t) == W) tickets->push_back(t);
+            else rest.push_back(t);
+        }
+        admitted->swap(rest);
+    } else {
+        const size_t n = std::min(admitted->size(), cap);
+        tickets->assign(admitted->begin(), admitted->begin() + (long)n);
+        admitted->erase(admitted->begin(), admitted->begin() + (long)n);
     }
 }
 

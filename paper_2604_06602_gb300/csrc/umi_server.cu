@@ -223,22 +223,9 @@ static void fail_requests_locked(umi_server *s, const std::vector<uint64_t> &tic
 static void launch_batch_locked(umi_server *s, int k, int32_t W0, std::unique_lock<std::mutex> &lk)
 {
     NvtxRange nvtx("umi server batch launch");
-    const size_t cap = (size_t)s->cfg.max_batch_curves;
     std::vector<uint64_t> tickets;
-    if (s->cfg.batch_by_window) {
-        // Requests of window length W0, in arrival order; the others keep theirs.
-        std::vector<uint64_t> rest;
-        rest.reserve(s->admitted.size());
-        for (uint64_t t : s->admitted) {
-            if (tickets.size() < cap && s->reqs[t]->W == W0) tickets.push_back(t);
-            else rest.push_back(t);
-        }
-        s->admitted.swap(rest);
-    } else {
-        const size_t n = std::min(s->admitted.size(), cap);
-        tickets.assign(s->admitted.begin(), s->admitted.begin() + n);
-        s->admitted.erase(s->admitted.begin(), s->admitted.begin() + n);
-    }
+    take_batch(&s->admitted, [s](uint64_t t) { return s->reqs[t]->W; }, W0, (size_t)s->cfg.max_batch_curves,
+               s->cfg.batch_by_window != 0, &tickets);
     const size_t take = tickets.size();
     struct Job {
         float *flux, *trend, *detr;
@@ -367,39 +354,14 @@ static void scheduler_main(umi_server *s)
         }
         bool launched = false;
         while (!hold && !s->admitted.empty() && !s->stop) {
-            // The window length to batch (the oldest admitted request's) and
-            // an idle stream for it.  With priority_window, long windows
-            // take only the low-priority half of the streams; when none of
-            // those is idle, the oldest short-window request goes first
-            // (short windows prefer the high-priority half).
-            const int n = (int)s->streams.size();
-            const int pw = s->cfg.priority_window;
-            auto idle = [&](int a, int b) {
-                for (int k = a; k < b; ++k)
-                    if (!s->inflight[k]) return k;
-                return -1;
-            };
-            int32_t W0 = s->reqs[s->admitted.front()]->W;
-            int k = -1;
-            if (pw <= 0) {
-                k = idle(0, n);
-            } else if (W0 >= pw) {
-                k = idle(n / 2, n);
-                if (k < 0) {
-                    W0 = -1;
-                    for (uint64_t t : s->admitted)
-                        if (s->reqs[t]->W < pw) {
-                            W0 = s->reqs[t]->W;
-                            break;
-                        }
-                }
-            }
-            if (pw > 0 && W0 >= 0 && W0 < pw) {
-                k = idle(0, n / 2);
-                if (k < 0) k = idle(n / 2, n);
-            }
-            if (k < 0 || W0 < 0) break;
-            launch_batch_locked(s, k, W0, lk);
+            // The window length to batch and an idle stream for it
+            // (choose_batch: oldest first; long windows on the low-priority
+            // half of the streams when priority_window is set).
+            const BatchChoice ch = choose_batch(
+                s->admitted, [s](uint64_t t) { return s->reqs[t]->W; },
+                [s](int k) { return !s->inflight[k]; }, (int)s->streams.size(), s->cfg.priority_window);
+            if (ch.stream < 0) break;
+            launch_batch_locked(s, ch.stream, ch.W, lk);
             launched = true;
         }
         if (launched) continue;
