@@ -271,8 +271,8 @@ def cpu_baseline(batch, W, budget_s=12.0):
         k = min(batch.B, int(k * max(2.0, budget_s / max(dt * threads, 1e-3))))
     evals, _ = window_work(sub.flux, sub.offsets, W[idx])
     return {"value": evals / dt, "unit": "window-evals/s", "cores": threads, "kind": "oracle",
-            "sample": "%d of the %d curves (FP64 C oracle, %d pthreads, %.1f s wall)"
-                      % (idx.size, batch.B, threads, dt),
+            "sample": "%d of the %d curves (FP64 C oracle, %d pthreads, %.1f s wall, %.0f core-s)"
+                      % (idx.size, batch.B, threads, dt, dt * threads),
             "curves_per_s": idx.size / dt}
 
 
