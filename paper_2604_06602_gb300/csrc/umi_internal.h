@@ -50,13 +50,29 @@ struct Plan {
     }
 };
 
+// Longest window a kernel variant covers.
+constexpr int kMaxWindow = 4095;
+
+// ---- planner (umi_plan.cu) ----
 bool legal_chain(int G, int chain);
+// Smallest legal chain of at least `target` positions; the shortest legal
+// chain; the longest chain the rule uses.
+int chain_at_least(int G, int64_t target);
+int shortest_chain(int G);
+int chain_cap(int G);
 // Regime of a band of `positions` windows of length W (positions <= 0: throughput).
 int plan_regime(int W, int64_t positions);
 // Plan for a band of `positions` windows of length W (positions <= 0: a band
 // large enough for the longest chain): the tuned plan for (W, regime) if any,
 // else the measured rule; the chain shrinks for small bands.
 umi_status make_plan(int W, int64_t positions, Plan *plan);
+// The plans umi_autotune times for a band of `positions` windows of length W.
+std::vector<Plan> autotune_candidates(int W, int64_t positions);
+// Records a tuned plan for (W, p.regime).
+void store_tuned(int W, const Plan &p);
+// Bumped by every change of the tuned-plan table (part of the graph-cache key).
+uint64_t tune_epoch();
+void plan_out(const Plan &p, umi_plan *out);
 umi_status check_params(const umi_params *p, umi_params *out);
 int resolve_min_valid(int W, int min_valid);
 // `flavour` = kFlagDiag | kFlagMad bits (the kernel build to use).
