@@ -118,12 +118,16 @@ static size_t request_bytes(int64_t n, bool device_input)
 
 static void CUDART_CB batch_done_cb(void *arg)
 {
+    // Once `done` is visible the scheduler may reap and free the batch, so it
+    // is set under the lock and the batch is not touched afterwards (the
+    // server outlives the callback: destroy synchronizes every stream).
     Batch *b = static_cast<Batch *>(arg);
-    b->t_done = now_s();
-    b->done.store(true);
     umi_server *s = b->srv;
+    const double t = now_s();
     {
         std::lock_guard<std::mutex> lk(s->mu);
+        b->t_done = t;
+        b->done.store(true);
     }
     s->cv_sched.notify_one();
 }
