@@ -377,10 +377,15 @@ umi_status umi_server_timeline(umi_server *s, uint64_t ticket, double *admit_s, 
 /* Blocks until the ticket is done or failed, or timeout_s passes. */
 umi_status umi_server_wait(umi_server *s, uint64_t ticket, double timeout_s);
 
-/* Copies a finished result to host buffers of n floats (either may be NULL). */
+/* Copies a finished result to host buffers of n floats (either may be NULL).
+ * UMI_ERR_NOT_READY / UMI_ERR_FAILED / UMI_ERR_UNKNOWN_TICKET as for poll.
+ * The copy runs after the server lock is dropped, so the ticket must not be
+ * released by another thread while it runs. */
 umi_status umi_server_copy_out(umi_server *s, uint64_t ticket, float *trend_h, float *detr_h);
 
-/* Frees the ticket's device memory; the pointers from poll become invalid. */
+/* Frees the ticket's device memory; the pointers from poll become invalid.
+ * Queued, admitted, done and failed tickets can be released (a queued or
+ * admitted one is withdrawn); UMI_ERR_NOT_READY while its batch runs. */
 umi_status umi_server_release(umi_server *s, uint64_t ticket);
 
 umi_status umi_server_get_stats(umi_server *s, umi_server_stats *out);
