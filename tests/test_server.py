@@ -111,6 +111,37 @@ def test_budget_backpressure(umi):
         assert srv.stats()["peak_resident_bytes"] <= 2 * per
 
 
+def test_withdraw_queued_requests(umi):
+    """Queued requests released before admission never run; the queue moves on
+    to the ones behind them once memory frees up."""
+    n = 20000
+    per = 3 * ((4 * n + 255) // 256 * 256)
+    xs = [synth.random_curve(170 + i, n) for i in range(6)]
+    with umi.Server(mem_budget_bytes=2 * per + 1024, n_streams=2) as srv:
+        tickets = [srv.submit(x, 361) for x in xs]
+        srv.wait(tickets[0], 60.0)
+        srv.wait(tickets[1], 60.0)
+        time.sleep(0.05)
+        assert srv.poll(tickets[2]) is None              # still queued: no memory
+        srv.release(tickets[3])                          # withdrawn while queued
+        srv.release(tickets[4])
+        for t in tickets[3:5]:
+            with pytest.raises(umi.UmiError) as e:
+                srv.poll(t)
+            assert e.value.status == umi.UMI_ERR_UNKNOWN_TICKET
+        for i in (0, 1):
+            srv.release(tickets[i])
+        for i in (2, 5):
+            srv.wait(tickets[i], 60.0)
+            tr, _ = srv.copy_out(tickets[i], n)
+            ta, _ = alone(umi, xs[i], 361)
+            assert np.array_equal(tr, ta, equal_nan=True)
+            srv.release(tickets[i])
+        st = srv.stats()
+        assert st["completed"] == 4 and st["admitted"] == 4 and st["released"] == 6
+        assert st["resident_bytes"] == 0 and st["queued_requests"] == 0
+
+
 def test_errors(umi):
     with umi.Server(mem_budget_bytes=1 << 20) as srv:
         x = synth.random_curve(1, 1000)
