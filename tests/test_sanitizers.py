@@ -35,9 +35,10 @@ def test_oracle_under_asan_and_ubsan(tmp_path):
 
 
 def test_host_pieces_under_asan_and_ubsan(tmp_path):
-    """The library's host-only pieces (the server's arena allocator and the
-    segmented entry point's gap scan, csrc/umi_host.h) built with the
-    sanitizers and checked against brute-force models."""
+    """The library's host-only pieces (csrc/umi_host.h: the server's arena
+    allocator and batching policy, the segmented entry point's gap scan) built
+    with the sanitizers and checked against brute-force models; the batching
+    policy runs inside a simulated serving loop with a mock launcher."""
     cxx = shutil.which("g++")
     if cxx is None:
         pytest.skip("g++ not available")
