@@ -321,46 +321,32 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
         if (__any_sync(0xffffffffu, need_full)) {
             // Bitwise binary search for the key of rank `target` among the S
             // slots (slots past W and missing samples hold kGap, whose key
-            // sorts below every sample's).  With few slots per lane the keys
-            // are computed once into registers from the window just loaded;
-            // otherwise each pass re-reads the window from shared memory (it
-            // runs once per chain), which keeps the registers free for the
-            // hot loops, and compares floats with the candidate's float:
-            // key order is float order for every non-NaN float except that
-            // -0 sorts below +0, and a candidate whose bits are a NaN is
-            // above (or below) every finite sample, so it compares as +inf
-            // (or -inf).  The -0/+0 case can only change the sign of a zero
+            // sorts below every sample's), over the window just loaded into
+            // registers.  With few slots per lane the keys are computed once
+            // into registers; otherwise each pass compares the slots' floats
+            // with the candidate key's float, which needs no key array: key
+            // order is float order for every non-NaN float except that -0
+            // sorts below +0, and a candidate whose bits are a NaN is above
+            // (or below) every finite sample, so it compares as +inf (or
+            // -inf).  The -0/+0 case can only change the sign of a zero
             // median, never its value or the counts that follow.
             constexpr bool kRegKeys = R <= 12;
             unsigned key[kRegKeys ? R : 1];
-            const int wb = q + glane;
-            int lim = W - glane;
-            asm volatile("" : "+r"(lim));
-            // Slot rows of this lane inside the window: G*i < lim.
-            const int rows = lim > 0 ? min(R, (lim + G - 1) / G) : 0;
             unsigned lo = 0xffffffffu, hi = 0u;
-            if constexpr (kRegKeys) {
 #pragma unroll
-                for (int k2 = 0; k2 < R / 2; ++k2) {
-                    key[2 * k2] = float_key(x[k2].x);
-                    key[2 * k2 + 1] = float_key(x[k2].y);
-                    if (x[k2].x > kGapLimit) {
-                        lo = min(lo, key[2 * k2]);
-                        hi = max(hi, key[2 * k2]);
-                    }
-                    if (x[k2].y > kGapLimit) {
-                        lo = min(lo, key[2 * k2 + 1]);
-                        hi = max(hi, key[2 * k2 + 1]);
-                    }
+            for (int k2 = 0; k2 < R / 2; ++k2) {
+                const unsigned ka = float_key(x[k2].x), kb = float_key(x[k2].y);
+                if constexpr (kRegKeys) {
+                    key[2 * k2] = ka;
+                    key[2 * k2 + 1] = kb;
                 }
-            } else {
-#pragma unroll 4
-                for (int i = 0; i < R; ++i) {
-                    const float v = tile[wb + G * i];
-                    const bool valid = (G * i < lim) && (v > kGapLimit);
-                    const unsigned kk = float_key(v);
-                    lo = valid ? min(lo, kk) : lo;
-                    hi = valid ? max(hi, kk) : hi;
+                if (x[k2].x > kGapLimit) {
+                    lo = min(lo, ka);
+                    hi = max(hi, ka);
+                }
+                if (x[k2].y > kGapLimit) {
+                    lo = min(lo, kb);
+                    hi = max(hi, kb);
                 }
             }
             lo = group_umin<G>(lo);
@@ -380,10 +366,9 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                 } else {
                     float candf = key_float(cand);
                     if (candf != candf) candf = (cand & 0x80000000u) ? INFINITY : -INFINITY;
-                    // Rows past W hold kGap: counted once, not read.
-#pragma unroll 4
-                    for (int i = 0; i < rows; ++i) c += (tile[wb + G * i] < candf) ? 1 : 0;
-                    c += (kGap < candf) ? R - rows : 0;
+#pragma unroll
+                    for (int k2 = 0; k2 < R / 2; ++k2)
+                        c += ((x[k2].x < candf) ? 1 : 0) + ((x[k2].y < candf) ? 1 : 0);
                 }
                 c = group_sum_int<G>(c);
                 if (c <= target) res = cand;
