@@ -37,7 +37,9 @@
  *     invalid argument returns UMI_ERR_INVALID_ARG and enqueues nothing.
  *     Errors are returned, never raised by abort().  umi_last_error() gives a
  *     message for the calling thread's most recent failure.
- *   - Calls are thread-safe.  Calls on different streams may overlap.
+ *   - Calls are thread-safe.  Calls on different streams may overlap, except
+ *     umi_detrend_batched_noalloc: all its calls share one device array, so
+ *     they must be ordered on one stream (or otherwise serialised).
  *   - umi_detrend_batched, umi_detrend_batched_host and umi_detrend_segmented
  *     keep their own CUDA-graph cache and stage their work tables through
  *     reused pinned host buffers; do not capture them into a graph of your
@@ -171,7 +173,11 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
  * UMI_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU loading libumi holds until
  * the process exits.  The caller still passes the input and output buffers.
  *   - It calls no cudaMalloc, cudaMallocAsync, cudaFree or other device
- *     allocator, and does not use the CUDA-graph cache.
+ *     allocator (nor cudaMallocHost), and does not use the CUDA-graph cache.
+ *   - The tables reach the array inside the parameters of small copy kernels
+ *     (one per 32,000 bytes of tables), enqueued on `stream` before the
+ *     detrend; a launch copies its parameters when it is enqueued, so the
+ *     call does not wait for earlier work on `stream` and returns at once.
  *   - A batch whose tables need more than UMI_NOALLOC_SCRATCH_BYTES returns
  *     UMI_ERR_INVALID_ARG with the size in umi_last_error(); 56 bytes per
  *     curve plus 8 bytes per tile, and a tile covers up to 544 positions at

@@ -15,6 +15,7 @@
 #include <cstring>
 #include <list>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -761,6 +762,26 @@ static umi_status time_plan(const Plan &plan, const float *flux, float *trend, f
 // up the device address once per device with cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[UMI_NOALLOC_SCRATCH_BYTES];
 
+// The tables reach the array inside kernel parameters: a launch copies its
+// parameters by value when it is enqueued, so the host's table buffer may be
+// freed at once and the call never waits for the stream (a cudaMemcpyAsync
+// from pageable memory may wait for all earlier work on the stream), and no
+// pinned staging buffer has to be allocated.  One chunk is just under the
+// 32,764-byte parameter limit of sm_70 and later GPUs.
+constexpr uint32_t kTableChunkWords = 8000;
+
+struct TableChunk {
+    uint32_t off_words;  // destination, in 4-byte words from the array's start
+    uint32_t n_words;    // words of `w` to copy, <= kTableChunkWords
+    uint32_t w[kTableChunkWords];
+};
+
+__global__ void noalloc_write_tables(uint32_t *dst, const TableChunk c)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c.n_words; i += gridDim.x * blockDim.x)
+        dst[c.off_words + i] = c.w[i];
+}
+
 static std::mutex g_noalloc_mu;
 static std::map<int, void *> g_noalloc_addr;  // device ordinal -> address of the array
 
@@ -827,16 +848,27 @@ static umi_status noalloc_batched(const float *flux, const int64_t *offsets, con
     void *dev = nullptr;
     st = noalloc_scratch_address(&dev);
     if (st != UMI_OK) return st;
-    std::vector<char> host(sc.counter_off);
-    memcpy(host.data() + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
-    memcpy(host.data() + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
-    // Stream-ordered after any earlier call's kernels on this stream; the
-    // pageable source may be freed once the call returns.
-    UMI_CUDA(cudaMemcpyAsync(dev, host.data(), sc.counter_off, cudaMemcpyHostToDevice, stream),
-             "cudaMemcpyAsync (no-alloc tables)");
+    // Host image of the tables (the scratch layout's offsets are multiples of
+    // 256 bytes, so it is a whole number of words).
+    std::vector<uint32_t> host(sc.counter_off / sizeof(uint32_t));
+    memcpy((char *)host.data() + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
+    memcpy((char *)host.data() + sc.item_off, lay.items.data(), lay.items.size() * sizeof(Item));
+    // Stream-ordered after any earlier call's kernels on this stream.
+    std::unique_ptr<TableChunk> chunk(new TableChunk);
+    int writers = 0;
+    for (size_t w0 = 0; w0 < host.size(); w0 += kTableChunkWords) {
+        const uint32_t nw = (uint32_t)std::min<size_t>(kTableChunkWords, host.size() - w0);
+        chunk->off_words = (uint32_t)w0;
+        chunk->n_words = nw;
+        memcpy(chunk->w, host.data() + w0, nw * sizeof(uint32_t));
+        noalloc_write_tables<<<(nw + 255) / 256, 256, 0, stream>>>((uint32_t *)dev, *chunk);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail_cuda(e, "no-alloc table write");
+        ++writers;
+    }
     int launches = 0;
     st = enqueue_bands(lay, (char *)dev, sc, stream, &launches);  // clears the counters first
-    g_kernel_launches += launches;
+    g_kernel_launches += writers + launches;
     return st;
 }
 

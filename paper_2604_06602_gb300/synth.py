@@ -90,8 +90,8 @@ def _flares(rng, t, count, amp, efold_days):
         return out
     starts = rng.uniform(t[0], t[-1], size=count)
     for ts in starts:
-        m = t >= ts
-        out[m] += amp * np.exp(-(t[m] - ts) / efold_days)
+        k = int(np.searchsorted(t, ts, side="left"))    # t is ascending: t >= ts from k on
+        out[k:] += amp * np.exp(-(t[k:] - ts) / efold_days)
     return out
 
 
@@ -226,45 +226,61 @@ def config4(seed: int = BASE_SEED + 3, n_curves: int = 256, n: int = 118000) -> 
 
 
 @dataclass
-class Request:
-    arrival_s: float
-    flux: np.ndarray
-    cadence: float
-    kind: str
+class ServingStream:
+    """A stream of detrend requests.  Request i arrives at ``arrivals[i] / rate``
+    seconds, is of class ``kind[i]`` (0 TESS 2-min, 1 Kepler 29.4-min, 2 TESS
+    20-s) and its flux is ``tapes[kind[i]][start[i]:start[i] + n[i]]``."""
+    arrivals: np.ndarray        # float64 [R], Poisson process of unit rate
+    kind: np.ndarray            # int8 [R]
+    n: np.ndarray               # int64 [R]
+    start: np.ndarray           # int64 [R]
+    tapes: list                 # three float32 arrays
+    cadences: tuple             # days, per class
+
+    def flux(self, i: int) -> np.ndarray:
+        k = int(self.kind[i])
+        return self.tapes[k][self.start[i]:self.start[i] + self.n[i]]
 
 
-def serving_requests(seed: int = BASE_SEED + 4, n_requests: int = 200000, rate_hz: float = 1e4,
-                     max_distinct: int = 512):
-    """Poisson arrivals at ``rate_hz``; sizes drawn from the mixture 45 % uneven
-    TESS, 45 % uneven Kepler, 10 % 20-s curves (N U(60k, 118k)).
+SERVING_CLASSES = (
+    # (share, N range, cadence, curve options): the mixture of the uneven
+    # TESS / Kepler batch and the 20-s large-window curves.
+    (0.45, (5000, 20000), CADENCE_TESS_2MIN, {}),
+    (0.45, (4000, 70000), CADENCE_KEPLER_LC, {"mid_gap_days": 0, "periodic_gap": (3.0, 90.0, 5.0)}),
+    (0.10, (60000, 118000), CADENCE_TESS_20S, {"spike_frac": 0.01}),
+)
 
-    To keep host memory bounded only ``max_distinct`` curves are generated; the
-    request stream cycles through them (sizes and cadences follow the same
-    mixture).  Returns (arrival times [s], list of pool curves, pool index per
-    request, cadence per pool curve, kind per pool curve).
-    """
+
+def serving_stream(seed: int = BASE_SEED + 4, n_requests: int = 200000,
+                   tape_samples=(8_000_000, 16_000_000, 8_000_000)) -> ServingStream:
+    """Poisson arrivals (unit rate) whose sizes are drawn from the full serving
+    mixture: 45 % TESS 2-min (N U(5k, 20k)), 45 % Kepler 29.4-min (N U(4k, 70k),
+    3-day gaps every 90 d) and 10 % TESS 20-s (N U(60k, 118k), 1 % spikes).
+    Every request gets its own size and its own slice of a long tape of curves
+    of its class (the tape is the class's light curves end to end), so no two
+    requests need be alike while host memory stays bounded."""
     rng = curve_rng(seed, 1 << 31)
-    gaps = rng.exponential(1.0 / rate_hz, size=n_requests)
-    arrivals = np.cumsum(gaps)
-    pool, cads, kinds = [], [], []
-    for i in range(max_distinct):
-        r = curve_rng(seed, i)
-        u = r.uniform()
-        if u < 0.45:
-            n = int(r.integers(5000, 20001))
-            f, _, _ = make_curve(r, n, CADENCE_TESS_2MIN)
-            pool.append(f); cads.append(CADENCE_TESS_2MIN); kinds.append("tess")
-        elif u < 0.90:
-            n = int(r.integers(4000, 70001))
-            f, _, _ = make_curve(r, n, CADENCE_KEPLER_LC, mid_gap_days=0,
-                                 periodic_gap=(3.0, 90.0, 5.0))
-            pool.append(f); cads.append(CADENCE_KEPLER_LC); kinds.append("kepler")
-        else:
-            n = int(r.integers(60000, 118001))
-            f, _, _ = make_curve(r, n, CADENCE_TESS_20S, spike_frac=0.01)
-            pool.append(f); cads.append(CADENCE_TESS_20S); kinds.append("tess20s")
-    which = rng.integers(0, max_distinct, size=n_requests)
-    return arrivals, pool, which, np.asarray(cads), kinds
+    arrivals = np.cumsum(rng.exponential(1.0, size=n_requests))
+    u = rng.uniform(size=n_requests)
+    shares = np.cumsum([c[0] for c in SERVING_CLASSES])
+    kind = np.searchsorted(shares, u, side="right").astype(np.int8)
+    kind = np.minimum(kind, len(SERVING_CLASSES) - 1)
+    lo = np.array([c[1][0] for c in SERVING_CLASSES], np.int64)
+    hi = np.array([c[1][1] for c in SERVING_CLASSES], np.int64)
+    n = rng.integers(lo[kind], hi[kind] + 1)
+    tapes = []
+    for k, (_, (nlo, nhi), cad, opts) in enumerate(SERVING_CLASSES):
+        parts, total, i = [], 0, 0
+        while total < tape_samples[k]:
+            r = curve_rng(seed, (k + 1) * 1_000_000 + i)
+            f, _, _ = make_curve(r, int(r.integers(nlo, nhi + 1)), cad, **opts)
+            parts.append(f)
+            total += f.size
+            i += 1
+        tapes.append(np.concatenate(parts)[:tape_samples[k]].astype(np.float32))
+    tape_len = np.array([t.size for t in tapes], np.int64)
+    start = np.floor(rng.uniform(size=n_requests) * (tape_len[kind] - n + 1)).astype(np.int64)
+    return ServingStream(arrivals, kind, n, start, tapes, tuple(c[2] for c in SERVING_CLASSES))
 
 
 def injection_base(seed, n_stars, mission="tess"):

@@ -227,6 +227,7 @@ def detrend(flux, W, p: Params | None = None, trend=None, detr=None, stream=None
     n = flux.numel()
     trend = torch.empty_like(flux) if trend is None else trend
     detr = torch.empty_like(flux) if detr is None else detr
+    _check_sizes(n, trend=trend, detr=detr)
     _check(load().umi_detrend(_dev_f32(flux, "flux"), n, int(W), None if p is None else ctypes.byref(p),
                               _dev_f32(trend, "trend"), _dev_f32(detr, "detr"), _stream_handle(stream)))
     return trend, detr
@@ -261,6 +262,22 @@ def _host_i32(a):
     return a, a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _check_sizes(total, **bufs):
+    """The C ABI takes bare pointers and cannot see buffer sizes: refuse, before
+    anything is launched, offsets that run past the flux buffer and outputs too
+    short for them (the kernels would read or write past their ends)."""
+    for name, b in bufs.items():
+        size = b.numel() if hasattr(b, "numel") else int(np.asarray(b).size)
+        if size < total:
+            raise ValueError("%s holds %d samples but the offsets (or n) need %d" % (name, size, total))
+
+
+def _csr_total(off):
+    if off.size < 1:
+        raise ValueError("offsets must hold B + 1 >= 1 entries")
+    return int(off.max())
+
+
 def detrend_batched(flux, offsets, W, p: Params | None = None, trend=None, detr=None, stream=None):
     """CSR batch on the GPU.  `offsets` [B+1] and `W` [B] are host arrays."""
     import torch
@@ -271,6 +288,7 @@ def detrend_batched(flux, offsets, W, p: Params | None = None, trend=None, detr=
         raise ValueError("W must have one entry per curve")
     trend = torch.empty_like(flux) if trend is None else trend
     detr = torch.empty_like(flux) if detr is None else detr
+    _check_sizes(_csr_total(off), flux=flux, trend=trend, detr=detr)
     _check(load().umi_detrend_batched(_dev_f32(flux, "flux"), offp, wp, B,
                                       None if p is None else ctypes.byref(p),
                                       _dev_f32(trend, "trend"), _dev_f32(detr, "detr"),
@@ -292,6 +310,7 @@ def detrend_batched_noalloc(flux, offsets, W, p: Params | None = None, trend=Non
         raise ValueError("W must have one entry per curve")
     trend = torch.empty_like(flux) if trend is None else trend
     detr = torch.empty_like(flux) if detr is None else detr
+    _check_sizes(_csr_total(off), flux=flux, trend=trend, detr=detr)
     _check(load().umi_detrend_batched_noalloc(_dev_f32(flux, "flux"), offp, wp, B,
                                               None if p is None else ctypes.byref(p),
                                               _dev_f32(trend, "trend"), _dev_f32(detr, "detr"),
@@ -311,6 +330,7 @@ def detrend_segmented(flux, offsets, W, p: Params | None = None, gap_min=0, min_
         raise ValueError("W must have one entry per curve")
     trend = torch.empty_like(flux) if trend is None else trend
     detr = torch.empty_like(flux) if detr is None else detr
+    _check_sizes(_csr_total(off), flux=flux, trend=trend, detr=detr)
     sp = SegmentParams(int(gap_min), int(min_seg))
     kept = ctypes.c_int64()
     _check(load().umi_detrend_segmented(_dev_f32(flux, "flux"), offp, wp, B,
@@ -338,10 +358,14 @@ def detrend_batched_host(flux, offsets, W, p: Params | None = None, trend=None, 
     off, offp = _host_i64(offsets)
     w, wp = _host_i32(W)
     B = off.size - 1
+    if w.size != B:
+        raise ValueError("W must have one entry per curve")
+    total = _csr_total(off)
     if trend is None:
-        trend = np.empty(int(off[-1]), np.float32)
+        trend = np.empty(total, np.float32)
     if detr is None:
-        detr = np.empty(int(off[-1]), np.float32)
+        detr = np.empty(total, np.float32)
+    _check_sizes(total, flux=flux, trend=trend, detr=detr)
     _check(load().umi_detrend_batched_host(host_ptr(flux, "flux"), offp, wp, B,
                                            None if p is None else ctypes.byref(p),
                                            host_ptr(trend, "trend"), host_ptr(detr, "detr"),

@@ -88,6 +88,36 @@ def test_host_validation_without_gpu(lib):
     assert st == umi.UMI_ERR_INVALID_ARG
 
 
+def test_binding_rejects_offsets_past_the_buffers():
+    """The C ABI cannot see buffer sizes, so the binding refuses offsets that
+    run past the flux buffer, or outputs shorter than the offsets need, before
+    it calls the library (on a GPU the kernels would read or write past the
+    buffers).  CPU tensors stand in for the device buffers: the size check
+    comes before the device-type check."""
+    torch = pytest.importorskip("torch")
+    flux = torch.ones(100)
+    short = torch.empty(50)
+    W = np.array([3, 3], np.int32)
+    over = np.array([0, 60, 120], np.int64)          # runs 20 samples past flux
+    fits = np.array([0, 30, 50], np.int64)
+    for fn in (umi.detrend_batched, umi.detrend_batched_noalloc):
+        with pytest.raises(ValueError, match="flux holds 100"):
+            fn(flux, over, W, trend=torch.empty(120), detr=torch.empty(120))
+        with pytest.raises(ValueError, match="trend holds 50"):
+            fn(flux, np.array([0, 30, 80], np.int64), W, trend=short, detr=torch.empty(100))
+    with pytest.raises(ValueError, match="detr holds 50"):
+        umi.detrend_segmented(flux, fits + np.array([0, 0, 30]), W, trend=torch.empty(100), detr=short)
+    with pytest.raises(ValueError, match="trend holds 50"):
+        umi.detrend(flux, 3, trend=short, detr=torch.empty(100))
+    # Host entry point: all buffers on the host, no GPU involved.
+    fh = np.ones(100, np.float32)
+    with pytest.raises(ValueError, match="flux holds 100"):
+        umi.detrend_batched_host(fh, over, W)
+    with pytest.raises(ValueError, match="detr holds 50"):
+        umi.detrend_batched_host(fh, np.array([0, 30, 80], np.int64), W,
+                                 trend=np.empty(80, np.float32), detr=np.empty(50, np.float32))
+
+
 def test_version(lib):
     assert "sm_103a" in umi.version()
 

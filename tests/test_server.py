@@ -284,3 +284,40 @@ def test_priority_config_checks(umi):
         t = srv.submit(x, 25)
         srv.wait(t, 60.0)
         srv.release(t)
+
+
+def test_served_results_match_oracle_on_serving_mixture(umi):
+    """The production library's server against the FP64 oracle on a sample of
+    the serving mixture (TESS 2-min, Kepler 29.4-min with gaps, TESS 20-s at
+    W = 2161): 300 host-buffer requests, each its own slice of a tape of its
+    class, submitted on a Poisson schedule at 20k/s so that they batch and
+    overlap on the GPU.  Sampled positions of every request are checked one by
+    one against the oracle (1e-5 relative, identical NaN pattern)."""
+    import oracle
+    from tests.helpers import compare_detr, compare_trend
+    st = synth.serving_stream(n_requests=300, tape_samples=(400_000, 800_000, 600_000))
+    Wk = [umi.window_length(c) for c in st.cadences]
+    W_req = np.array(Wk, np.int32)[st.kind]
+    assert set(np.unique(st.kind).tolist()) == {0, 1, 2}
+    arrivals = st.arrivals / 20000.0
+    rng = np.random.default_rng(5)
+    with umi.Server(mem_budget_bytes=4 << 30, n_streams=4, max_batch_curves=64) as srv:
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(st.n.size):
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            tickets.append(srv.submit(st.flux(i), int(W_req[i])))
+        for t in tickets:
+            srv.wait(t, 120.0)
+        assert srv.stats()["batches_launched"] < len(tickets)      # requests were batched
+        for i, t in enumerate(tickets):
+            x = st.flux(i)
+            tr, de = srv.copy_out(t, x.size)
+            srv.release(t)
+            n, W = x.size, int(W_req[i])
+            h = (W - 1) // 2
+            pos = np.unique(np.concatenate([[0, n - 1, h, n - 1 - h], rng.integers(0, n, 12)]))
+            ref = oracle.detrend_positions(x, W, pos)
+            compare_trend(tr[pos], ref["trend"], what="request %d" % i)
+            compare_detr(de[pos], ref["detr"], what="request %d" % i)
