@@ -46,7 +46,8 @@ struct Plan {
     int tile() const { return (32 / G) * chain; }
     size_t smem_bytes() const
     {
-        return sizeof(float) * (size_t)(threads / 32) * (size_t)(tile() + G * R - 1);
+        return sizeof(float) * (size_t)(threads / 32) *
+               (size_t)(tile() + G * R - 1 + (stages_outputs(G) ? tile() : 0));
     }
 };
 

@@ -252,9 +252,16 @@ struct MedianState {
 // Kernel flags: diagnostic outputs, MAD scale instead of Eq. 1.
 enum : int { kFlagDiag = 1, kFlagMad = 2 };
 
+// Narrow groups (G <= 4 lanes per window) stage their trend values in the
+// warp's shared-memory slice and write trend and detrended flux at the end of
+// the tile, coalesced: their 32/G groups walk chains a whole chain apart, so a
+// direct store from every group would touch 32/G separate DRAM sectors with
+// 4 bytes each.  The slice then holds T more floats after the staged samples.
+__host__ __device__ constexpr bool stages_outputs(int G) { return G <= 4; }
+
 template <int G, int R, int FLAGS>
 __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, const TileRef tile,
-                                              int64_t t0, int q0, int P, int glane)
+                                              float *out, int64_t t0, int q0, int P, int glane)
 {
     constexpr int S = G * R;
     const int W = cv.W;
@@ -520,8 +527,12 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
 
         if (glane == 0 && p < cv.n) {
             const float nanv = __int_as_float(0x7fc00000);
-            cv.trend[p] = produce ? mu : nanv;
-            cv.detr[p] = produce ? __fdiv_rn(centre, mu) : nanv;
+            if constexpr (stages_outputs(G)) {
+                out[q] = produce ? mu : nanv;  // written out by the tile's flush
+            } else {
+                cv.trend[p] = produce ? mu : nanv;
+                cv.detr[p] = produce ? __fdiv_rn(centre, mu) : nanv;
+            }
             if constexpr ((FLAGS & kFlagDiag) != 0) {
                 if (dg.median) dg.median[p] = (st.nv >= 1) ? st.m : nanv;
                 if (dg.nvalid) dg.nvalid[p] = st.nv;
@@ -536,7 +547,8 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
 // positions (plus the S-1 halo samples) in its slice of shared memory, so no
 // CTA-wide barrier is ever needed.  Without a queue, warp w of CTA b takes
 // item b*warps + w; with a queue, each warp pulls items until none is left.
-// Dynamic shared memory: warps * (T + S - 1) floats.  MINB (CTAs of 256
+// Dynamic shared memory: warps * (T + S - 1) floats, plus warps * T for the
+// staged trend when stages_outputs(G).  MINB (CTAs of 256
 // threads per SM) sets the register budget the compiler aims for.  FLAGS
 // selects the diagnostic outputs and the MAD scale; every curve of one launch
 // must have the scale mode the kernel was built for.
@@ -553,12 +565,14 @@ __global__ void __launch_bounds__(256, MINB) umi_tile_kernel(LaunchArgs a)
     const int P = a.chain;
     const int T = (32 / G) * P;
     const int tile_len = T + S - 1;
-    float *tile = smem + (size_t)warp * tile_len;
+    const int slice_len = tile_len + (stages_outputs(G) ? T : 0);
+    float *tile = smem + (size_t)warp * slice_len;
+    float *out = tile + tile_len;  // staged trend of the tile's positions (narrow groups)
 #ifdef UMI_CHECKED
     {
         unsigned dsm;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
-        if ((uint64_t)n_warps * (uint64_t)tile_len * sizeof(float) > dsm) {
+        if ((uint64_t)n_warps * (uint64_t)slice_len * sizeof(float) > dsm) {
             if (threadIdx.x == 0 && a.check) atomicOr(a.check, kCheckSmemSize);
             return;
         }
@@ -605,8 +619,20 @@ __global__ void __launch_bounds__(256, MINB) umi_tile_kernel(LaunchArgs a)
             tile[k] = v;
         }
         __syncwarp();
-        process_chain<G, R, FLAGS>(cv, a.diag, tref, t0, group * P, P, glane);
+        process_chain<G, R, FLAGS>(cv, a.diag, tref, out, t0, group * P, P, glane);
         __syncwarp();  // every lane is done with the tile before it is restaged
+        if constexpr (stages_outputs(G)) {
+            // Flush: position k of the tile has its sample at tile[k + h];
+            // a NaN trend (no estimate) gives a NaN quotient too.
+            const float nanv = __int_as_float(0x7fc00000);
+            const int kend = (int)min((int64_t)T, cv.n - t0);
+            for (int k = lane; k < kend; k += 32) {
+                const float mu = out[k];
+                cv.trend[t0 + k] = mu;
+                cv.detr[t0 + k] = (mu == mu) ? __fdiv_rn(tref[k + h], mu) : nanv;
+            }
+            __syncwarp();  // the flush reads the tile: done before it is restaged
+        }
         if (!a.queue) break;
     }
 }
