@@ -8,8 +8,9 @@
 //
 // GPU design (not the paper's one-thread-per-window kernel, Section 2.6):
 //  * A warp owns a tile of T consecutive positions of one curve and stages the
-//    T + S - 1 samples its windows touch into its slice of shared memory once;
-//    missing samples (non-finite, or outside the curve) become kGap.
+//    T + S - 1 samples its windows touch into its slice of shared memory once,
+//    with 4-byte cp.async copies; missing samples (non-finite, or outside the
+//    curve) become kGap.
 //  * A "group" of G lanes (G = 1..32, a power of two) evaluates one window at a
 //    time, each lane holding R window slots in registers (S = G*R >= W slots;
 //    slots past W hold kGap).  The 32/G groups of a warp run in lock step on
@@ -189,6 +190,17 @@ __device__ __forceinline__ float eq_flag(float a, float b)
     asm("set.eq.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
     return d;
 }
+
+// 4-byte asynchronous copy from global to shared memory (cp.async): the copy
+// is issued without waiting for it, so a lane's staging loads are all in
+// flight at once; cp_async_wait_all waits for the calling thread's copies.
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gmem_src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Order-preserving map from non-NaN floats to unsigned keys (-0 sorts just
 // below +0; the counts that follow compare floats, where they are equal).
@@ -609,15 +621,17 @@ __global__ void __launch_bounds__(256, MINB) umi_tile_kernel(LaunchArgs a)
         }
 #endif
 
+        // Stage with asynchronous 4-byte copies (no alignment beyond the
+        // float's), then turn the non-finite samples each lane copied into
+        // the gap marker; slots outside the curve get it directly.
         for (int k = lane; k < tile_len; k += 32) {
             const int64_t idx = t0 - h + k;
-            float v = kGap;
-            if (idx >= 0 && idx < cv.n) {
-                const float f = __ldg(cv.flux + idx);
-                if (isfinite(f)) v = f;
-            }
-            tile[k] = v;
+            if (idx >= 0 && idx < cv.n) cp_async4(tile + k, cv.flux + idx);
+            else tile[k] = kGap;
         }
+        cp_async_wait_all();
+        for (int k = lane; k < tile_len; k += 32)
+            if (!isfinite(tile[k])) tile[k] = kGap;
         __syncwarp();
         process_chain<G, R, FLAGS>(cv, a.diag, tref, out, t0, group * P, P, glane);
         __syncwarp();  // every lane is done with the tile before it is restaged
