@@ -25,10 +25,13 @@ namespace umi {
 bool legal_chain(int G, int chain)
 {
     // The 32/G groups of a warp start `chain` positions apart in the tile, so
-    // their G-lane loads hit banks (g * chain + lane) mod 32; a chain of
-    // G * (odd number) positions keeps the groups on disjoint banks.
+    // one slot row's loads read words g * chain + lane (g < 32/G, lane < G).
+    // A chain of G * (odd number) positions keeps the groups on disjoint
+    // banks; a chain of at most G makes the groups' words one contiguous run
+    // of at most 32 (overlapping windows read the same words), so no two
+    // distinct words share a bank either.
     if (chain < 1) return false;
-    if (G >= 32) return true;
+    if (G >= 32 || chain <= G) return true;
     return chain % G == 0 && ((chain / G) & 1) == 1;
 }
 
@@ -222,7 +225,9 @@ umi_status make_plan(int W, int64_t positions, Plan *plan)
 // most a third of W (the smallest covering capacity always qualifies) -- in
 // the latency regime also the 32-lane variants within 2W --, two CTA sizes,
 // and chains of about 8 to 136 positions plus a third, half, once, twice and
-// three times the chain the rule gives for this band.
+// three times the chain the rule gives for this band; in the latency regime
+// groups narrower than a warp also try chains shorter than G (1, 2, 4, 6),
+// which give a warp several windows in flight at once.
 std::vector<Plan> autotune_candidates(int W, int64_t positions)
 {
     const int regime = plan_regime(W, positions);
@@ -245,6 +250,9 @@ std::vector<Plan> autotune_candidates(int W, int64_t positions)
                 std::find(chains.begin(), chains.end(), c) == chains.end())
                 chains.push_back(c);
         }
+        if (regime == kRegimeLatency && G < 32)
+            for (int c : {1, 2, 4, 6})
+                if (c < G && std::find(chains.begin(), chains.end(), c) == chains.end()) chains.push_back(c);
         for (int threads : {128, 256}) {
             for (int c : chains) {
                 Plan p;

@@ -389,6 +389,32 @@ def test_every_variant_forced(umi, tmp_path, variant):
         umi.clear_tuning()
 
 
+@pytest.mark.parametrize("variant", [(2, 32, 3), (4, 32, 3), (8, 46, 2), (16, 24, 4)])
+def test_short_chains_forced(umi, tmp_path, variant):
+    """Chains shorter than the group width (the groups of a warp then walk
+    overlapping windows) for each narrow variant, forced through tuning lines
+    in both regimes, against the oracle with gaps and a ragged tail."""
+    G, R, M = variant
+    S = G * R
+    gpu = torch.cuda.get_device_name()
+    try:
+        for chain in sorted({1, max(1, G // 2), G - 1}):
+            W = S - 2 if (S - 2) % 2 else S - 3
+            f = tmp_path / "short.txt"
+            f.write_text("".join("%s|%d|%s|%d|%d|%d|%d|128\n" % (gpu, W, r, G, R, M, chain)
+                                 for r in ("throughput", "latency")))
+            umi.clear_tuning()
+            umi.load_tuning(str(f))
+            n = 37 * (32 // G) * chain + 2 * W + 13
+            pl = umi.get_plan(W, n)
+            assert (pl["lanes"], pl["slots"], pl["chain"]) == (G, R, chain)
+            x = synth.random_curve(9100 + S + chain, n, nan_runs=2, run_len=(1, W))
+            compare_diag(run_diag(umi, x, W), oracle.detrend(x, W),
+                         what="short chain %d %s W=%d" % (chain, variant, W))
+    finally:
+        umi.clear_tuning()
+
+
 def test_stream_ordering_on_side_stream(umi):
     x = synth.config1().curve(0)[:5000].copy()
     s = torch.cuda.Stream()
