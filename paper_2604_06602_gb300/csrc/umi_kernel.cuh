@@ -183,6 +183,14 @@ __device__ __forceinline__ float ge_flag(float a, float b)
     return d;
 }
 
+// 1.0f when a <= b, else 0.0f (also 0.0f when either is NaN).
+__device__ __forceinline__ float le_flag(float a, float b)
+{
+    float d;
+    asm("set.le.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
 // 1.0f when a == b, else 0.0f.
 __device__ __forceinline__ float eq_flag(float a, float b)
 {
@@ -338,17 +346,22 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
 
         // ---- exact radix select (chain start / restart) --------------------
         if (__any_sync(0xffffffffu, need_full)) {
-            // Bitwise binary search for the key of rank `target` among the S
-            // slots (slots past W and missing samples hold kGap, whose key
-            // sorts below every sample's), over the window just loaded into
-            // registers.  With few slots per lane the keys are computed once
-            // into registers; otherwise each pass compares the slots' floats
-            // with the candidate key's float, which needs no key array: key
-            // order is float order for every non-NaN float except that -0
-            // sorts below +0, and a candidate whose bits are a NaN is above
-            // (or below) every finite sample, so it compares as +inf (or
-            // -inf).  The -0/+0 case can only change the sign of a zero
-            // median, never its value or the counts that follow.
+            // Binary search over the integer keys for the key of rank
+            // `target` among the S slots (slots past W and missing samples
+            // hold kGap, whose key sorts below every sample's), over the
+            // window just loaded into registers: the smallest key v with
+            // more than `target` slots at or below it, which is always a
+            // sample's key.  It bisects the interval [min, max] of the valid
+            // samples' keys, so it takes ceil(log2(max - min + 1)) passes (a
+            // window of flux around 1.0, whose keys differ from bit 23 on
+            // because 1.0 starts a binade, spans only about 2^17 keys).
+            // With few slots per lane the keys are computed once into
+            // registers; otherwise each pass compares the slots' floats with
+            // the midpoint's float, which needs no key array: between two
+            // finite keys every key is a finite float, and key order is
+            // float order except that -0 sorts below +0, which can only
+            // change the sign of a zero median, never its value or the counts
+            // that follow.
             constexpr bool kRegKeys = R <= 12;
             unsigned key[kRegKeys ? R : 1];
             unsigned lo = 0xffffffffu, hi = 0u;
@@ -370,29 +383,35 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             }
             lo = group_umin<G>(lo);
             hi = group_umax<G>(hi);
-            const unsigned diff = lo ^ hi;
-            const int nbits = diff ? 32 - __clz((int)diff) : 0;
-            unsigned res = (nbits >= 32) ? 0u : (lo & ~((1u << nbits) - 1u));
             const int target = (S - st.nv) + k;  // rank among all S slots
-            const int nb = (int)__reduce_max_sync(0xffffffffu, (unsigned)(need_full ? nbits : 0));
 #pragma unroll 1
-            for (int b = nb - 1; b >= 0; --b) {
-                const unsigned cand = res | (1u << b);
+            while (__any_sync(0xffffffffu, need_full && lo < hi)) {
+                const unsigned mid = lo + ((hi - lo) >> 1);
                 int c = 0;
                 if constexpr (kRegKeys) {
 #pragma unroll
-                    for (int i = 0; i < R; ++i) c += (key[i] < cand) ? 1 : 0;
+                    for (int i = 0; i < R; ++i) c += (key[i] <= mid) ? 1 : 0;
                 } else {
-                    float candf = key_float(cand);
-                    if (candf != candf) candf = (cand & 0x80000000u) ? INFINITY : -INFINITY;
+                    const float midf = key_float(mid);
+                    if constexpr (R >= 32) {
+                        // 0/1 float flags summed with FADD2 (exact: at most R < 2^24),
+                        // so half of a long pass runs on the FMA pipe.
+                        float2 cf = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int k2 = 0; k2 < R / 2; ++k2)
-                        c += ((x[k2].x < candf) ? 1 : 0) + ((x[k2].y < candf) ? 1 : 0);
+                        for (int k2 = 0; k2 < R / 2; ++k2)
+                            cf = __fadd2_rn(cf, make_float2(le_flag(x[k2].x, midf), le_flag(x[k2].y, midf)));
+                        c = (int)(cf.x + cf.y);
+                    } else {
+#pragma unroll
+                        for (int k2 = 0; k2 < R / 2; ++k2)
+                            c += ((x[k2].x <= midf) ? 1 : 0) + ((x[k2].y <= midf) ? 1 : 0);
+                    }
                 }
                 c = group_sum_int<G>(c);
-                if (c <= target) res = cand;
+                if (c > target) hi = mid;
+                else lo = mid + 1;
             }
-            const float mf = key_float(res);
+            const float mf = key_float(lo);
             int cl = 0, ce = 0;
 #pragma unroll
             for (int k = 0; k < R / 2; ++k) {
