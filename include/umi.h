@@ -125,8 +125,9 @@ umi_status umi_detrend(const float *flux_d, int64_t n, int32_t W, const umi_para
  *   params     shared by all curves; NULL means defaults
  * Device scratch (the work queue, a few bytes per tile) comes from the
  * stream-ordered allocator (cudaMallocAsync) on `stream` and is released on
- * the same stream.  Asynchronous on `stream`.  Equal-shaped batches replay a
- * cached CUDA graph (see umi_set_graph_cache).
+ * the same stream.  Asynchronous on `stream`.  Equal-shaped batches of two or
+ * more curves replay a cached CUDA graph (see umi_set_graph_cache); a batch
+ * with one non-empty curve is one direct launch and needs no scratch.
  */
 umi_status umi_detrend_batched(const float *flux_d, const int64_t *offsets_h, const int32_t *W_h,
                                int32_t B, const umi_params *params, float *trend_d,

@@ -567,10 +567,9 @@ static umi_status build_graph(const std::vector<Curve> &curves, GraphEntry *g)
         st = prepare_kernel(band.plan, band.flavour);
         if (st != UMI_OK) return st;
     }
-    // One curve needs no tables: the graph holds its kernel alone.
-    const bool one = curves.size() == 1;
+    // Batches of two or more curves only (one curve launches directly).
     const Scratch sc = scratch_layout(curves.size(), lay.items.size(), lay.bands.size());
-    if (!one) {
+    {
         std::vector<char> host(sc.counter_off);
         memcpy(host.data() + sc.curve_off, curves.data(), curves.size() * sizeof(Curve));
         if (!lay.items.empty())
@@ -586,8 +585,7 @@ static umi_status build_graph(const std::vector<Curve> &curves, GraphEntry *g)
         cudaStreamDestroy(cs);
         return fail_cuda(e, "cudaStreamBeginCapture");
     }
-    umi_status est = one ? launch_single_curve(curves[0], curves[0].n, nullptr, cs, &g->launches)
-                         : enqueue_bands(lay, (char *)g->dev, sc, cs, &g->launches);
+    umi_status est = enqueue_bands(lay, (char *)g->dev, sc, cs, &g->launches);
     e = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
     if (est != UMI_OK) {
@@ -634,7 +632,9 @@ static umi_status batched_impl(const float *flux, const int64_t *offsets, const 
         if (n == 0) continue;
         curves.push_back(make_curve(flux + o, trend + o, detr + o, n, W[b], p));
     }
-    if (!allow_graph || plan_sizes || !g_graph_enabled.load()) {
+    // One curve launches directly: it needs no device tables, and a graph
+    // holding its one kernel costs about 1 us more on the GPU than a launch.
+    if (!allow_graph || plan_sizes || !g_graph_enabled.load() || curves.size() == 1) {
         int launches = 0;
         st = launch_curve_table(curves, stream, &launches, plan_sizes);
         g_kernel_launches += launches;
@@ -861,8 +861,12 @@ static umi_status noalloc_batched(const float *flux, const int64_t *offsets, con
         chunk->off_words = (uint32_t)w0;
         chunk->n_words = nw;
         memcpy(chunk->w, host.data() + w0, nw * sizeof(uint32_t));
-        noalloc_write_tables<<<(nw + 255) / 256, 256, 0, stream>>>((uint32_t *)dev, *chunk);
-        cudaError_t e = cudaGetLastError();
+        // The argument array points at the heap chunk, so the 32 KB parameter
+        // is copied into the launch from there (no stack copy on the host).
+        uint32_t *dst = (uint32_t *)dev;
+        void *args[] = {&dst, chunk.get()};
+        cudaError_t e = cudaLaunchKernel((const void *)noalloc_write_tables, dim3((nw + 255) / 256), dim3(256),
+                                         args, 0, stream);
         if (e != cudaSuccess) return fail_cuda(e, "no-alloc table write");
         ++writers;
     }
