@@ -16,8 +16,8 @@
 //    slots past W hold kGap).  The 32/G groups of a warp run in lock step on
 //    neighbouring chains; every block that shuffles is entered warp-uniformly.
 //  * Each group walks a chain of P consecutive positions.  At the chain start
-//    (or after an empty window) the median comes from an exact bitwise radix
-//    select on order-preserving integer keys.  Afterwards the group keeps the
+//    (or after an empty window) the median comes from an exact binary search
+//    over order-preserving integer keys.  Afterwards the group keeps the
 //    counts L = #{x < m}, E = #{x == m}, G+ = #{x > m} of the current window
 //    and updates them in O(1) per step from the sample that leaves and the one
 //    that enters.  One step moves the median's rank by at most one, so the new
@@ -344,7 +344,7 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             else if (k >= st.L + st.E) move = -1;
         }
 
-        // ---- exact radix select (chain start / restart) --------------------
+        // ---- exact selection by key bisection (chain start / restart) -------
         if (__any_sync(0xffffffffu, need_full)) {
             // Binary search over the integer keys for the key of rank
             // `target` among the S slots (slots past W and missing samples
