@@ -396,11 +396,16 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                     if constexpr (R >= 32) {
                         // 0/1 float flags summed with FADD2 (exact: at most R < 2^24),
                         // so half of a long pass runs on the FMA pipe.
-                        float2 cf = make_float2(0.f, 0.f);
+                        // Two accumulators (even and odd pairs) halve the
+                        // dependent chain; the count is exact in any order.
+                        float2 cf0 = make_float2(0.f, 0.f), cf1 = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int k2 = 0; k2 < R / 2; ++k2)
-                            cf = __fadd2_rn(cf, make_float2(le_flag(x[k2].x, midf), le_flag(x[k2].y, midf)));
-                        c = (int)(cf.x + cf.y);
+                        for (int k2 = 0; k2 < R / 2; ++k2) {
+                            const float2 fl = make_float2(le_flag(x[k2].x, midf), le_flag(x[k2].y, midf));
+                            if (k2 & 1) cf1 = __fadd2_rn(cf1, fl);
+                            else cf0 = __fadd2_rn(cf0, fl);
+                        }
+                        c = (int)((cf0.x + cf0.y) + (cf1.x + cf1.y));
                     } else {
 #pragma unroll
                         for (int k2 = 0; k2 < R / 2; ++k2)
@@ -440,21 +445,27 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             const float2 sg2 = make_float2(sg, sg);
             const float sm = sg * st.m;
             const float2 push = make_float2(-0x1p127f, -0x1p127f);
-            float best = -INFINITY;
+            // Even and odd pairs keep separate maxima and tie counts (exact in
+            // any order), which halves the dependent chains of both scans.
+            float best0 = -INFINITY, best1 = -INFINITY;
 #pragma unroll
             for (int k = 0; k < R / 2; ++k) {
                 const float2 y = __fmul2_rn(x[k], sg2);
                 const float2 f = make_float2(ge_flag(y.x, sm), ge_flag(y.y, sm));
                 const float2 yb = __ffma2_rn(f, push, y);
-                best = fmaxf(best, fmaxf(yb.x, yb.y));
+                if (k & 1) best1 = fmaxf(best1, fmaxf(yb.x, yb.y));
+                else best0 = fmaxf(best0, fmaxf(yb.x, yb.y));
             }
-            best = group_max<G>(best);
+            float best = group_max<G>(fmaxf(best0, best1));
             const float cand = sg * best;
-            float2 ef = make_float2(0.f, 0.f);
+            float2 ef0 = make_float2(0.f, 0.f), ef1 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < R / 2; ++k)
-                ef = __fadd2_rn(ef, make_float2(eq_flag(x[k].x, cand), eq_flag(x[k].y, cand)));
-            const int e = group_sum_int<G>((int)(ef.x + ef.y));
+            for (int k = 0; k < R / 2; ++k) {
+                const float2 fl = make_float2(eq_flag(x[k].x, cand), eq_flag(x[k].y, cand));
+                if (k & 1) ef1 = __fadd2_rn(ef1, fl);
+                else ef0 = __fadd2_rn(ef0, fl);
+            }
+            const int e = group_sum_int<G>((int)((ef0.x + ef0.y) + (ef1.x + ef1.y)));
             if (move > 0) {
                 st.Gp += st.E;
                 st.L -= e;

@@ -2,7 +2,8 @@
 sampled oracle check the benchmark reports for every workload accepts the
 oracle's own outputs and rejects a planted error; steady-state latency
 percentiles drop the first second; the serving stream follows its mixture and
-every request's flux is a slice inside its class's tape."""
+every request's flux is a slice inside its class's tape; the kernel code hash
+that keys the measured traffic ignores comments."""
 import numpy as np
 
 import bench
@@ -67,3 +68,16 @@ def test_serving_stream_mixture_and_slices():
     x = st.flux(7)
     assert x.dtype == np.float32 and x.size == st.n[7]
     assert np.isnan(st.tapes[1]).any()                              # Kepler tapes carry gaps
+
+
+def test_kernel_code_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """The measured-traffic record is keyed by a hash of the kernel's code:
+    comment and blank-line edits keep it, any code edit changes it."""
+    src = tmp_path / "k.cuh"
+    src.write_text("// header\nint f(int x)\n{\n    return x + 1;  /* one */\n}\n")
+    monkeypatch.setattr(bench, "KERNEL_SOURCE", str(src))
+    h0 = bench.kernel_sha256()
+    src.write_text("// another header\n\nint f(int x)\n{\n    /* a\n       block */\n    return x + 1;  // one\n}\n")
+    assert bench.kernel_sha256() == h0
+    src.write_text("// header\nint f(int x)\n{\n    return x + 2;  /* one */\n}\n")
+    assert bench.kernel_sha256() != h0
