@@ -181,9 +181,9 @@ umi_status umi_detrend_batched_host(const float *flux_h, const int64_t *offsets_
  *     call does not wait for earlier work on `stream` and returns at once.
  *   - A batch whose tables need more than UMI_NOALLOC_SCRATCH_BYTES returns
  *     UMI_ERR_INVALID_ARG with the size in umi_last_error(); 56 bytes per
- *     curve plus 8 bytes per tile, and a tile covers up to 544 positions at
- *     W = 361 (roughly 12,000 curves of 18,000 samples); split larger
- *     batches.
+ *     curve plus 8 bytes per tile, and a tile covers 288 to 544 positions at
+ *     W = 361 depending on the plan (roughly 7,500 to 12,000 curves of
+ *     18,000 samples); split larger batches.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
