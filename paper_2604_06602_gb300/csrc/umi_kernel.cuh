@@ -27,11 +27,12 @@
 //  * Eq. 1 is one pass over the registers, G+ comes from the counts.
 //  * Phase 3 keeps y = x - m in registers, in pairs for the packed FP32x2
 //    instructions, and runs the fixed number of steps on mu = m + delta: per
-//    slot u_eff = min(y kp - delta kp, y kn - delta kn) (kp = 1/(c s),
-//    kn = alpha/(c s): Eq. 2 without a branch), z = sat(1 - u_eff^2),
-//    w = z^2 (Eq. 3), and delta = sum(w y)/sum(w) (Eq. 4 about m).  A kGap
-//    slot has |u_eff| >= 1 (or it overflows), so sat() makes its weight
-//    exactly 0 without a mask.
+//    slot u_eff^2 = t (t + rho |t|) with t = sigma (y - delta) (for
+//    1/4 <= alpha <= 4; otherwise u_eff = min(y kp - delta kp, y kn - delta
+//    kn) with kp = 1/(c s), kn = alpha/(c s): Eq. 2 without a branch either
+//    way), z = sat(1 - u_eff^2), w = z^2 (Eq. 3), and delta = sum(w y)/sum(w)
+//    (Eq. 4 about m).  A kGap slot has u_eff^2 >= 1 (or it overflows, or is
+//    NaN), so sat() makes its weight exactly 0 without a mask.
 #pragma once
 
 #include <cstdint>
@@ -288,6 +289,16 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
     const int h = (W - 1) >> 1;
     const float alpha = cv.alpha;
     const float cst = cv.c;
+    // Sign select of Eq. 2 through |t| (Phase 3): rho = (1 - alpha^2)/(1 +
+    // alpha^2) and sigma = sgp/(c s).  The branch on the small side is t (1 -
+    // |rho|), a difference, so rho's rounding (at most 3 units of roundoff)
+    // grows by (a^2 - 1)/2 there, a = max(alpha, 1/alpha).  This form serves
+    // 1/4 <= alpha <= 4, where u_eff^2 stays within 12 + 1.5 (a^2 - 1) units
+    // (2e-6 relative at a = 4); every other alpha takes the min of two scaled
+    // residuals.
+    const bool abs_form = alpha >= 0.25f && alpha <= 4.f;
+    const float rho = fmaf(-alpha, alpha, 1.f) / fmaf(alpha, alpha, 1.f);
+    const float sgp = sqrtf(0.5f * fmaf(alpha, alpha, 1.f));
     const int iters = cv.iters;
     const bool tail_only = G * (R - 2) <= W;  // rows 0..R-3 hold only slots < W
     static_assert(R % 2 == 0, "slots are processed in pairs");
@@ -529,39 +540,67 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
             }
             const bool iterate = produce && (s > 0.f);
             if (__any_sync(0xffffffffu, iterate)) {
-                // u_eff of Eq. 2 is min(y kp - delta kp, y kn - delta kn) with
-                // kp = 1/(c s), kn = alpha/(c s) when alpha >= 1 (max when
-                // alpha < 1; negating both keeps one code path, and only u_eff^2
-                // is used).  Eq. 4 in centred form: delta_new = sum(w y)/sum(w)
-                // since mu = m + delta.
+                // Eq. 2 needs only u_eff^2 = k^2 (y - delta)^2 with k = kp =
+                // 1/(c s) above the trend and k = kn = alpha/(c s) below it.
+                // Eq. 4 in centred form: delta_new = sum(w y)/sum(w), since
+                // mu = m + delta.
                 const float inv = 1.f / (cst * s);
-                const float flip = (alpha >= 1.f) ? 1.f : -1.f;
-                const float kp = flip * inv;
-                const float kn = flip * alpha * inv;
-                const float2 kp2 = make_float2(kp, kp);
-                const float2 kn2 = make_float2(kn, kn);
                 float delta = 0.f;
+                if (abs_form) {
+                    // t = sigma (y - delta), sigma^2 = (kp^2 + kn^2)/2:
+                    // t (t + rho |t|) = kp^2 u^2 for u >= 0, kn^2 u^2 for u < 0,
+                    // so one FMA with |t| as an operand does the sign select.
+                    const float sg = inv * sgp;
+                    const float2 sg2 = make_float2(sg, sg);
 #pragma unroll 1
-                for (int it = 0; it < iters; ++it) {
-                    const float2 c1 = make_float2(-delta * kp, -delta * kp);
-                    const float2 c2 = make_float2(-delta * kn, -delta * kn);
-                    float2 swt = make_float2(0.f, 0.f), swyt = make_float2(0.f, 0.f);
+                    for (int it = 0; it < iters; ++it) {
+                        const float2 c0 = make_float2(-delta * sg, -delta * sg);
+                        float2 swt = make_float2(0.f, 0.f), swyt = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int k = 0; k < R / 2; ++k) {
-                        const float2 p1 = __ffma2_rn(x[k], kp2, c1);
-                        const float2 p2 = __ffma2_rn(x[k], kn2, c2);
-                        const float qa = fminf(p1.x, p2.x);
-                        const float qb = fminf(p1.y, p2.y);
-                        const float2 z = make_float2(fma_sat(-qa, qa, 1.f), fma_sat(-qb, qb, 1.f));
-                        const float2 w = __fmul2_rn(z, z);
-                        swt = __fadd2_rn(swt, w);
-                        swyt = __ffma2_rn(w, x[k], swyt);
+                        for (int k = 0; k < R / 2; ++k) {
+                            const float2 ts = __ffma2_rn(x[k], sg2, c0);
+                            const float va = fmaf(rho, fabsf(ts.x), ts.x);
+                            const float vb = fmaf(rho, fabsf(ts.y), ts.y);
+                            const float2 z = make_float2(fma_sat(-ts.x, va, 1.f), fma_sat(-ts.y, vb, 1.f));
+                            const float2 w = __fmul2_rn(z, z);
+                            swt = __fadd2_rn(swt, w);
+                            swyt = __ffma2_rn(w, x[k], swyt);
+                        }
+                        const float sws = group_sum<G>(swt.x + swt.y);
+                        const float swys = group_sum<G>(swyt.x + swyt.y);
+                        // sws <= S, so the fast quotient (2 ulp) is safe here;
+                        // its error is far below the FP32 rounding of the sums.
+                        if (sws > 0.f) delta = __fdividef(swys, sws);
                     }
-                    const float sws = group_sum<G>(swt.x + swt.y);
-                    const float swys = group_sum<G>(swyt.x + swyt.y);
-                    // sws <= S, so the fast quotient (2 ulp) is safe here; its
-                    // error is far below the FP32 rounding of the sums.
-                    if (sws > 0.f) delta = __fdividef(swys, sws);
+                } else {
+                    // u_eff = min(y kp - delta kp, y kn - delta kn) when
+                    // alpha >= 1 (max when alpha < 1; negating both keeps one
+                    // code path).
+                    const float flip = (alpha >= 1.f) ? 1.f : -1.f;
+                    const float kp = flip * inv;
+                    const float kn = flip * alpha * inv;
+                    const float2 kp2 = make_float2(kp, kp);
+                    const float2 kn2 = make_float2(kn, kn);
+#pragma unroll 1
+                    for (int it = 0; it < iters; ++it) {
+                        const float2 c1 = make_float2(-delta * kp, -delta * kp);
+                        const float2 c2 = make_float2(-delta * kn, -delta * kn);
+                        float2 swt = make_float2(0.f, 0.f), swyt = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int k = 0; k < R / 2; ++k) {
+                            const float2 p1 = __ffma2_rn(x[k], kp2, c1);
+                            const float2 p2 = __ffma2_rn(x[k], kn2, c2);
+                            const float qa = fminf(p1.x, p2.x);
+                            const float qb = fminf(p1.y, p2.y);
+                            const float2 z = make_float2(fma_sat(-qa, qa, 1.f), fma_sat(-qb, qb, 1.f));
+                            const float2 w = __fmul2_rn(z, z);
+                            swt = __fadd2_rn(swt, w);
+                            swyt = __ffma2_rn(w, x[k], swyt);
+                        }
+                        const float sws = group_sum<G>(swt.x + swt.y);
+                        const float swys = group_sum<G>(swyt.x + swyt.y);
+                        if (sws > 0.f) delta = __fdividef(swys, sws);
+                    }
                 }
                 if (iterate) mu = m + delta;
             }

@@ -100,6 +100,19 @@ def test_all_missing_constant_and_sparse(umi, W):
                  what="sparse min_valid=0 W=%d" % W)
 
 
+@pytest.mark.parametrize("alpha", [0.2, 0.25, 4.0, 4.5])
+def test_sign_select_forms_at_their_boundary(umi, alpha):
+    """The iteration loop selects the Eq. 2 branch through |t| for
+    1/4 <= alpha <= 4 and by the min of two scaled residuals otherwise: both
+    sides of both edges against the oracle, on flux-like data with flares and
+    dips and on a gappy noise curve."""
+    x = synth.config1().curve(0)[:6000].copy()
+    p = umi.params(alpha=alpha)
+    compare_diag(run_diag(umi, x, 361, p), oracle.detrend(x, 361, alpha=alpha), what="alpha=%g" % alpha)
+    y = synth.random_curve(77, 3000, nan_frac=0.05, nan_runs=2, run_len=(1, 61))
+    compare_diag(run_diag(umi, y, 61, p), oracle.detrend(y, 61, alpha=alpha), what="gappy alpha=%g" % alpha)
+
+
 @pytest.mark.parametrize("preset", [(2.0, 5.0), (3.0, 5.0), (1.0, 5.0), (10.0, 2.5), (0.5, 4.0)])
 def test_parameter_presets(umi, preset):
     """Table 4 presets (and alpha < 1) on flux-like data with flares and dips."""
