@@ -46,8 +46,8 @@ LANES_PER_SM = 128
 # headline workload, from the ncu capture of that workload, valid only while
 # the kernel's code (comments and blank lines removed) hashes to
 # `kernel_sha256`.
-MEASURED_TRAFFIC = {"bytes": 162.79e6,
-                    "kernel_sha256": "9ad90fcff4387d9565c7a19375cde61f5225ab0a3e86041fa60ab08cfb86a380"}
+MEASURED_TRAFFIC = {"bytes": 164.30e6,
+                    "kernel_sha256": "44a48bf4fb36654cecb76cc36f1eaf196e7d25beacfe12dadee93ddafdc20443"}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2604_06602_gb300", "csrc", "umi_kernel.cuh")
 
 

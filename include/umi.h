@@ -274,12 +274,16 @@ umi_status umi_get_plan(int32_t W, int64_t positions, umi_plan *plan);
 /*
  * Autotuner.  Times every eligible (lanes, slots, chain, threads) choice for
  * window length W on a synthetic flux-like curve of `positions` samples on
- * `stream` (blocking), and records the fastest for W in the regime of that
- * band size (see umi_plan: latency or throughput); later bands of W in the
- * same regime use it (a band smaller than `positions` gets the planner's own
- * chain for its size times the ratio the tuner preferred at `positions`, if
- * that is shorter).  umi_save_tuning / umi_load_tuning persist the table
- * as text lines "gpu|W|regime|G|R|MINB|chain|threads|positions" (regime
+ * `stream` (blocking; every launch is timed alone, as one call runs, and
+ * each choice's time is the best of three timed runs, a run repeating a
+ * short plan for about a millisecond and counting the mean; `best_ms` is
+ * that time), and records the fastest for
+ * W in the regime of that band size (see umi_plan: latency or throughput);
+ * later bands of W in the same regime use it (a band smaller than
+ * `positions` gets the planner's own chain for its size times the ratio the
+ * tuner preferred at `positions`, if that is shorter).  umi_save_tuning /
+ * umi_load_tuning persist the table as text lines
+ * "gpu|W|regime|G|R|MINB|chain|threads|positions" (regime
  * "latency" or "throughput"; a line without the regime field is a throughput
  * plan; without `positions`, smaller bands get the planner's own chain when
  * it is shorter) keyed by GPU name (MINB: the register budget of the

@@ -738,15 +738,27 @@ static umi_status time_plan(const Plan &plan, const float *flux, float *trend, f
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // Every launch is timed alone (events around it, the host waiting for
+    // it), as one call runs.  The first run warms up and the second sizes
+    // the timed runs: a plan that takes microseconds (one curve) is near the
+    // event timer's resolution, so a run repeats it for about a millisecond
+    // and counts the mean; the best of three timed runs is the plan's time.
     double best = 1e30;
-    for (int rep = 0; rep < 4 && st == UMI_OK; ++rep) {
-        cudaEventRecord(e0, stream);
-        st = enqueue_bands(lay, (char *)dev, sc, stream, nullptr);
-        cudaEventRecord(e1, stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(UMI_ERR_CUDA, "autotune run failed");
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        if (rep > 0) best = std::min(best, (double)t);  // first run warms up
+    int reps_per_run = 1;
+    for (int run = 0; run < 5 && st == UMI_OK; ++run) {
+        double sum = 0.0;
+        for (int r = 0; r < reps_per_run && st == UMI_OK; ++r) {
+            cudaEventRecord(e0, stream);
+            st = enqueue_bands(lay, (char *)dev, sc, stream, nullptr);
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(UMI_ERR_CUDA, "autotune run failed");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            sum += t;
+        }
+        const double mean = sum / reps_per_run;
+        if (run == 1) reps_per_run = (int)std::min(64.0, std::max(1.0, std::floor(1.0 / std::max(mean, 1e-3))));
+        if (run >= 2) best = std::min(best, mean);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
