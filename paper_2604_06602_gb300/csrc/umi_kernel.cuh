@@ -296,9 +296,12 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
     // 1/4 <= alpha <= 4, where u_eff^2 stays within 12 + 1.5 (a^2 - 1) units
     // (2e-6 relative at a = 4); every other alpha takes the min of two scaled
     // residuals.
+    // With r = 1/sqrt(msq) (Phase 2), sigma = r k1 in that form, and in the
+    // other kp = r k1, kn = alpha kp (k1 negated when alpha < 1).
     const bool abs_form = alpha >= 0.25f && alpha <= 4.f;
     const float rho = fmaf(-alpha, alpha, 1.f) / fmaf(alpha, alpha, 1.f);
-    const float sgp = sqrtf(0.5f * fmaf(alpha, alpha, 1.f));
+    const float k1 = (abs_form ? sqrtf(0.5f * fmaf(alpha, alpha, 1.f)) : (alpha >= 1.f ? 1.f : -1.f)) /
+                     (kScaleFactor * cst);
     const int iters = cv.iters;
     const bool tail_only = G * (R - 2) <= W;  // rows 0..R-3 hold only slots < W
     static_assert(R % 2 == 0, "slots are processed in pairs");
@@ -507,7 +510,13 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                 s2 = __ffma2_rn(yp, yp, s2);
             }
             const float s2sum = group_sum<G>(s2.x + s2.y);
-            s = (st.Gp > 0) ? kScaleFactor * sqrtf(s2sum / (float)st.Gp) : 0.f;
+            // msq = S2 / n+ and s = 0.6745 sqrt(msq) (Eq. 1).  The iterations
+            // take 1/(c s) as rsqrt(msq) / (0.6745 c): a fast quotient and an
+            // approximate reciprocal square root, 2 ulp each, far below what
+            // the trend resolves, in place of an IEEE quotient, root and
+            // reciprocal.  A subnormal mean square takes the IEEE root.
+            const float msq = (st.Gp > 0) ? __fdividef(s2sum, (float)st.Gp) : 0.f;
+            s = kScaleFactor * sqrtf(msq);  // for the diagnostic output
             if constexpr ((FLAGS & kFlagMad) != 0) {
                 // MAD = the order statistic of rank floor((nv-1)/2) of |y| over
                 // the valid slots, by bisection on the bit patterns of
@@ -538,19 +547,21 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                 }
                 s = __uint_as_float(res);
             }
-            const bool iterate = produce && (s > 0.f);
+            const bool iterate = produce && ((FLAGS & kFlagMad) != 0 ? (s > 0.f) : (msq > 0.f));
             if (__any_sync(0xffffffffu, iterate)) {
                 // Eq. 2 needs only u_eff^2 = k^2 (y - delta)^2 with k = kp =
                 // 1/(c s) above the trend and k = kn = alpha/(c s) below it.
                 // Eq. 4 in centred form: delta_new = sum(w y)/sum(w), since
                 // mu = m + delta.
-                const float inv = 1.f / (cst * s);
+                float r;  // 0.6745 / s
+                if constexpr ((FLAGS & kFlagMad) != 0) r = kScaleFactor / s;
+                else r = (msq >= 0x1p-126f) ? rsqrtf(msq) : 1.f / sqrtf(msq);
                 float delta = 0.f;
                 if (abs_form) {
                     // t = sigma (y - delta), sigma^2 = (kp^2 + kn^2)/2:
                     // t (t + rho |t|) = kp^2 u^2 for u >= 0, kn^2 u^2 for u < 0,
                     // so one FMA with |t| as an operand does the sign select.
-                    const float sg = inv * sgp;
+                    const float sg = r * k1;
                     const float2 sg2 = make_float2(sg, sg);
 #pragma unroll 1
                     for (int it = 0; it < iters; ++it) {
@@ -576,9 +587,8 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                     // u_eff = min(y kp - delta kp, y kn - delta kn) when
                     // alpha >= 1 (max when alpha < 1; negating both keeps one
                     // code path).
-                    const float flip = (alpha >= 1.f) ? 1.f : -1.f;
-                    const float kp = flip * inv;
-                    const float kn = flip * alpha * inv;
+                    const float kp = r * k1;
+                    const float kn = alpha * kp;
                     const float2 kp2 = make_float2(kp, kp);
                     const float2 kn2 = make_float2(kn, kn);
 #pragma unroll 1
