@@ -46,8 +46,8 @@ LANES_PER_SM = 128
 # headline workload, from the ncu capture of that workload, valid only while
 # the kernel's code (comments and blank lines removed) hashes to
 # `kernel_sha256`.
-MEASURED_TRAFFIC = {"bytes": 164.30e6,
-                    "kernel_sha256": "44a48bf4fb36654cecb76cc36f1eaf196e7d25beacfe12dadee93ddafdc20443"}
+MEASURED_TRAFFIC = {"bytes": 162.56e6,
+                    "kernel_sha256": "edc71fe8871a4e0ef2db61c1899a6ad528431d2ff780337c5303920567a2e102"}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2604_06602_gb300", "csrc", "umi_kernel.cuh")
 
 
