@@ -132,15 +132,22 @@ def lpt_part(batch, W, rank, world):
     return batch.subset(idx), W[idx], idx
 
 
-def tune_for_batch(umi, batch, W):
-    """The kernel plans the benchmark times: for each window length, tuned at
-    about the batch's own size (the best chain length depends on it), and,
-    where one curve alone is a latency-regime band, at a median curve."""
+def tune_for_batch(umi, batch, W, flux):
+    """The kernel plans the benchmark times: for each window length, tuned on
+    the band's own curves (`flux`, the batch on the device; every k-th curve
+    when they hold more than 2e7 positions, repeated when they hold fewer
+    than 1e6: the best plan depends on the band's size, on how its curves end
+    within tiles and on its data), and, where one curve alone is a
+    latency-regime band, on a single synthetic curve of the median length."""
+    import torch
     for w in sorted(set(W.tolist())):
-        n_w = int(batch.lengths[W == w].sum())
-        umi.autotune(int(w), positions=max(1_000_000, min(n_w, 20_000_000)))
-        n_one = int(np.median(batch.lengths[W == w]))
-        if n_one > 0 and umi.get_plan(int(w), n_one)["latency"]:
+        idx = np.flatnonzero(W == w)
+        n_one = max(1, int(np.median(batch.lengths[idx])))
+        pick = idx[::max(1, int(np.ceil(batch.lengths[idx].sum() / 20_000_000)))]
+        reps = max(1, int(np.ceil(1_000_000 / batch.lengths[pick].sum())))
+        parts = [flux[int(batch.offsets[i]):int(batch.offsets[i + 1])] for i in pick] * reps
+        umi.autotune_batch(int(w), np.tile(batch.lengths[pick], reps), flux=torch.cat(parts))
+        if umi.get_plan(int(w), n_one)["latency"]:
             umi.autotune(int(w), positions=n_one)
 
 
@@ -378,7 +385,7 @@ def run_umi(args):
     if args.tuning_file:
         umi.load_tuning(args.tuning_file)
     else:
-        tune_for_batch(umi, batch, W)
+        tune_for_batch(umi, batch, W, flux)
     tuned_plan = {int(w): umi.get_plan(int(w), int(batch.lengths[W == w].sum())) for w in sorted(set(W.tolist()))}
     if args.save_tuning and rank == 0:
         umi.save_tuning(args.save_tuning)
@@ -556,9 +563,9 @@ def workload_leg(umi, torch, dev, flush, name, local):
     batch, desc = make_workload(SimpleNamespace(workload=name, curves=None, n=18000, shard="own"), 0)
     W = np.array([umi.window_length(c) for c in batch.cadence], np.int32)
     steps = {"c1": 20, "c3": 5, "c4": 3}[name]
-    tune_for_batch(umi, batch, W)
     evals, samples = window_work(batch.flux, batch.offsets, W)
     flux = torch.from_numpy(batch.flux).to(dev)
+    tune_for_batch(umi, batch, W, flux)
     trend = torch.empty_like(flux)
     detr = torch.empty_like(flux)
     peak_ops, peak_note = lane_op_peak(torch, dev)

@@ -276,8 +276,9 @@ umi_status umi_get_plan(int32_t W, int64_t positions, umi_plan *plan);
  * window length W on a synthetic flux-like curve of `positions` samples on
  * `stream` (blocking; every launch is timed alone, as one call runs, and
  * each choice's time is the best of three timed runs, a run repeating a
- * short plan for about a millisecond and counting the mean; `best_ms` is
- * that time), and records the fastest for
+ * short plan for about a millisecond and counting the mean; the choices
+ * within 3 % of the fastest get three more rounds; `best_ms` is the chosen
+ * plan's time), and records the fastest for
  * W in the regime of that band size (see umi_plan: latency or throughput);
  * later bands of W in the same regime use it (a band smaller than
  * `positions` gets the planner's own chain for its size times the ratio the
@@ -293,6 +294,21 @@ umi_status umi_get_plan(int32_t W, int64_t positions, umi_plan *plan);
  */
 umi_status umi_autotune(int32_t W, int64_t positions, void *stream, umi_plan *best,
                         double *best_ms);
+
+/* Autotuner on a batch: as umi_autotune, with every choice timed on a batch
+ * of `n_curves` curves of window W whose lengths are curve_len_h[0..n_curves)
+ * (host array, read during the call; one band of their total positions,
+ * which sets the regime and the size the plan is tuned at), so the tile
+ * rounding at each curve's end, the work queue's tail and the data's own
+ * gaps and outliers count as they do in such a batch.  flux_d: the curves'
+ * samples back to back on the device (read only, and only by the calls'
+ * launches on `stream`), or NULL for synthetic flux-like noise.  A single
+ * long curve of noise shows none of these: for many short curves of uneven
+ * length a shorter chain can be faster than the one such a curve of the
+ * same total length prefers.  Every length >= 1 and their sum <= 2^31, else
+ * UMI_ERR_INVALID_ARG. */
+umi_status umi_autotune_batch(int32_t W, const float *flux_d, const int64_t *curve_len_h,
+                              int32_t n_curves, void *stream, umi_plan *best, double *best_ms);
 umi_status umi_save_tuning(const char *path);
 umi_status umi_load_tuning(const char *path);
 void umi_clear_tuning(void);

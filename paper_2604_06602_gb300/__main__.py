@@ -73,6 +73,9 @@ def main(argv=None):
     t = sub.add_parser("tune", help="autotune the plan for a window length and band size")
     t.add_argument("W", type=int)
     t.add_argument("positions", type=int)
+    t.add_argument("--curve-len", type=int, default=None,
+                   help="tune on curves of this many samples (positions / curve-len of them) "
+                        "instead of one curve of `positions` samples")
     t.add_argument("--save", default=None, help="write the tuning table to this file")
     args = ap.parse_args(argv)
 
@@ -82,7 +85,10 @@ def main(argv=None):
         print(json.dumps(umi.get_plan(args.W, args.positions)))
         return 0
     if args.cmd == "tune":
-        plan, ms = umi.autotune(args.W, positions=args.positions)
+        if args.curve_len:
+            plan, ms = umi.autotune_batch(args.W, [args.curve_len] * max(1, args.positions // args.curve_len))
+        else:
+            plan, ms = umi.autotune(args.W, positions=args.positions)
         print(json.dumps({"plan": plan, "ms": ms}))
         if args.save:
             umi.save_tuning(args.save)

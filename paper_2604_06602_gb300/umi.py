@@ -36,7 +36,7 @@ STATUS_NAMES = {0: "UMI_OK", 1: "UMI_ERR_INVALID_ARG", 2: "UMI_ERR_CUDA", 3: "UM
 EXPORTS = [
     "umi_default_params", "umi_window_length", "umi_detrend", "umi_detrend_batched",
     "umi_detrend_batched_host", "umi_detrend_batched_noalloc", "umi_detrend_diag", "umi_max_window", "umi_get_plan",
-    "umi_autotune", "umi_save_tuning", "umi_load_tuning", "umi_clear_tuning",
+    "umi_autotune", "umi_autotune_batch", "umi_save_tuning", "umi_load_tuning", "umi_clear_tuning",
     "umi_set_graph_cache", "umi_server_default_config", "umi_server_create", "umi_server_submit",
     "umi_server_poll", "umi_server_wait", "umi_server_copy_out", "umi_server_release",
     "umi_server_get_stats", "umi_server_inject_fault", "umi_server_destroy", "umi_last_error",
@@ -128,6 +128,7 @@ def load(build_if_missing: bool = False):
             "umi_max_window": (_i32, []),
             "umi_get_plan": (ctypes.c_int, [_i32, _i64, P(Plan)]),
             "umi_autotune": (ctypes.c_int, [_i32, _i64, _vp, P(Plan), P(ctypes.c_double)]),
+            "umi_autotune_batch": (ctypes.c_int, [_i32, _vp, _vp, _i32, _vp, P(Plan), P(ctypes.c_double)]),
             "umi_save_tuning": (ctypes.c_int, [ctypes.c_char_p]),
             "umi_load_tuning": (ctypes.c_int, [ctypes.c_char_p]),
             "umi_clear_tuning": (None, []),
@@ -384,6 +385,27 @@ def autotune(W, positions=2_000_000, stream=None):
     ms = ctypes.c_double()
     _check(load().umi_autotune(int(W), int(positions), _stream_handle(stream), ctypes.byref(pl),
                                ctypes.byref(ms)))
+    return pl.as_dict(), ms.value
+
+
+def autotune_batch(W, curve_lengths, flux=None, stream=None):
+    """Tune W's plan on a batch of curves of the given lengths (the tile
+    rounding at every curve's end counts): the curves in `flux` (a CUDA
+    float32 tensor holding them back to back), or synthetic noise."""
+    lens = np.ascontiguousarray(curve_lengths, np.int64)
+    if lens.ndim != 1 or lens.size == 0:
+        raise ValueError("curve_lengths must be a non-empty 1-D sequence")
+    ptr = None
+    if flux is not None:
+        import torch
+        if flux.dtype != torch.float32 or not flux.is_cuda or not flux.is_contiguous():
+            raise ValueError("flux must be a contiguous float32 CUDA tensor")
+        _check_sizes(int(lens.sum()), flux=flux)
+        ptr = flux.data_ptr()
+    pl = Plan()
+    ms = ctypes.c_double()
+    _check(load().umi_autotune_batch(int(W), ptr, lens.ctypes.data_as(ctypes.c_void_p), int(lens.size),
+                                     _stream_handle(stream), ctypes.byref(pl), ctypes.byref(ms)))
     return pl.as_dict(), ms.value
 
 

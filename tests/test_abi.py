@@ -86,6 +86,15 @@ def test_host_validation_without_gpu(lib):
     st = lib.umi_detrend_batched(buf, off.ctypes.data_as(ctypes.c_void_p),
                                  W.ctypes.data_as(ctypes.c_void_p), 2, None, buf, buf, None)
     assert st == umi.UMI_ERR_INVALID_ARG
+    # The autotuners check the window and the tuning batch's shape first.
+    for W_, lens in ((360, [1000] * 4), (361, [1000, 0, 5]), (361, [1000, -3]), (361, [1 << 30] * 3),
+                     (0, [10]), (361, [])):
+        arr = np.array(lens + [7], np.int64)
+        assert lib.umi_autotune_batch(W_, None, arr.ctypes.data_as(ctypes.c_void_p), len(lens),
+                                      None, None, None) == umi.UMI_ERR_INVALID_ARG
+    assert lib.umi_autotune_batch(361, None, None, 3, None, None, None) == umi.UMI_ERR_INVALID_ARG
+    assert lib.umi_autotune(360, 1000, None, None, None) == umi.UMI_ERR_INVALID_ARG
+    assert lib.umi_autotune(361, 0, None, None, None) == umi.UMI_ERR_INVALID_ARG
 
 
 def test_binding_rejects_offsets_past_the_buffers():

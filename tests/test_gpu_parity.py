@@ -135,7 +135,9 @@ def test_zero_centred_and_scaled(umi):
     """Curves centred on zero and far from unit scale; the trend bound is
     1e-5 of max(|trend|, c s) here."""
     rng = np.random.default_rng(77)
-    for level, sigma in ((0.0, 1.0), (0.0, 1e-6), (1e4, 30.0), (-5.0, 0.1)):
+    # sigma 5e-20: the squared residuals of Eq. 1 are subnormal (about 2.5e-39),
+    # so the mean square takes the kernel's IEEE root instead of rsqrt.
+    for level, sigma in ((0.0, 1.0), (0.0, 1e-6), (1e4, 30.0), (-5.0, 0.1), (0.0, 5e-20)):
         x = (level + sigma * rng.standard_normal(3000)).astype(np.float32)
         x[rng.uniform(size=x.size) < 0.03] = np.nan
         compare_diag(run_diag(umi, x, 129), oracle.detrend(x, 129), scale_aware=True,
@@ -336,6 +338,34 @@ def test_autotune_keeps_parity(umi, tmp_path):
         assert umi.get_plan(361, -1)["chain"] == plan["chain"]
         xs = synth.random_curve(91, 12500)
         compare_diag(run_diag(umi, xs, 361), oracle.detrend(xs, 361), what="tuned latency plan")
+    finally:
+        umi.clear_tuning()
+
+
+def test_autotune_batch_keeps_parity(umi):
+    """Plans tuned on a batch (its own curves, or synthetic curves of its
+    lengths) are throughput plans, become the band's plan, and keep parity on
+    that batch; the tuner leaves the caller's flux untouched."""
+    try:
+        b = synth.config3(n_curves=48)
+        W = np.array([umi.window_length(c) for c in b.cadence], np.int32)
+        lens = np.diff(b.offsets)
+        flux = torch.from_numpy(b.flux).cuda()
+        tess = np.flatnonzero(W == 361)
+        own = torch.cat([flux[int(b.offsets[i]):int(b.offsets[i + 1])] for i in tess] * 8)
+        before = own.clone()
+        plan, ms = umi.autotune_batch(361, np.tile(lens[tess], 8), flux=own)
+        torch.cuda.synchronize()
+        assert torch.equal(own.isnan(), before.isnan()) and torch.equal(own.nan_to_num(), before.nan_to_num())
+        assert plan["latency"] == 0 and ms > 0 and plan["lanes"] * plan["slots"] >= 361
+        assert umi.get_plan(361, -1)["chain"] == plan["chain"]
+        kplan, _ = umi.autotune_batch(25, np.tile(lens[W == 25], 8))
+        assert kplan["latency"] == 0 and kplan["lanes"] * kplan["slots"] >= 25
+        tr, de = umi.detrend_batched(flux, b.offsets, W)
+        torch.cuda.synchronize()
+        rt, rd = oracle.detrend_batch(b.flux, b.offsets, W)
+        compare_trend(tr.cpu().numpy(), rt, what="batch-tuned config3")
+        compare_detr(de.cpu().numpy(), rd, what="batch-tuned config3")
     finally:
         umi.clear_tuning()
 
