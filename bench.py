@@ -794,8 +794,14 @@ def serving_leg(umi, torch, dev, args):
     Wk = [umi.window_length(c) for c in st.cadences]
     W_req = np.array(Wk, np.int32)[st.kind]
     for k, w in enumerate(Wk):
-        # Both regimes: large batches, and a median request of this window length.
-        umi.autotune(w, positions=2_000_000)
+        # Both regimes: large batches, tuned on the class's own first requests
+        # (up to 450 of them, about a saturated batch, and 2e7 positions), and
+        # a median request of this window length.
+        idx = np.flatnonzero(st.kind == k)[:450]
+        idx = idx[np.cumsum(st.n[idx]) <= 20_000_000]
+        flux_k = torch.cat([torch.from_numpy(st.flux(int(i))) for i in idx]).to(dev)
+        umi.autotune_batch(w, st.n[idx], flux=flux_k)
+        del flux_k
         n_one = int(np.median(st.n[st.kind == k]))
         if umi.get_plan(w, n_one)["latency"]:
             umi.autotune(w, positions=n_one)
