@@ -44,8 +44,8 @@ def test_full_size_batch_sampled(umi, workload):
     W = np.array([umi.window_length(c) for c in b.cadence], np.int32)
     try:
         umi.clear_tuning()
-        bench.tune_for_batch(umi, b, W)
         flux = torch.from_numpy(b.flux).cuda()
+        bench.tune_for_batch(umi, b, W, flux)
         tr, de = umi.detrend_batched(flux, b.offsets, W)
         torch.cuda.synchronize()
         tr, de = tr.cpu().numpy(), de.cpu().numpy()

@@ -189,7 +189,7 @@ def config2(umi):
     flux = torch.from_numpy(b.flux).cuda()
     try:
         umi.clear_tuning()
-        bench.tune_for_batch(umi, b, W)
+        bench.tune_for_batch(umi, b, W, flux)
         tr, de = umi.detrend_batched(flux, b.offsets, W)
         torch.cuda.synchronize()
     finally:
