@@ -730,8 +730,10 @@ static umi_status time_plan(const Plan &plan, const float *flux, float *trend, f
     lay.bands[0].plan = plan;
     lay.bands[0].first_item = 0;
     const int64_t T = plan.tile();
-    for (size_t c = 0; c < lengths.size(); ++c)
-        for (int64_t k = 0; k < (lengths[c] + T - 1) / T; ++k) lay.items.push_back(Item{(int32_t)c, (int32_t)k});
+    for (size_t c = 0; c < lengths.size(); ++c) {
+        const int64_t tiles = (lengths[c] + T - 1) / T;
+        for (int64_t k = 0; k < tiles; ++k) lay.items.push_back(Item{(int32_t)c, (int32_t)k});
+    }
     lay.bands[0].n_items = (int32_t)lay.items.size();
     umi_status st = prepare_kernel(plan, 0);
     if (st != UMI_OK) return st;
