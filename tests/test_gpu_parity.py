@@ -370,6 +370,28 @@ def test_autotune_batch_keeps_parity(umi):
         umi.clear_tuning()
 
 
+def test_autotune_batch_tiny_curves(umi):
+    """Curves shorter than, equal to and just past the window, each a
+    single partial tile: a latency-regime band whose tuned plan serves such a
+    batch with parity."""
+    try:
+        lens = np.array([1, 3, 24, 25, 26, 60], np.int64)
+        plan, ms = umi.autotune_batch(25, lens)
+        assert plan["latency"] == 1 and ms > 0 and plan["lanes"] * plan["slots"] >= 25
+        assert umi.get_plan(25, int(lens.sum())) == plan
+        xs = [synth.random_curve(300 + i, int(n), nan_frac=0.1) for i, n in enumerate(lens)]
+        flux = np.concatenate(xs).astype(np.float32)
+        off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        W = np.full(lens.size, 25, np.int32)
+        tr, de = umi.detrend_batched(torch.from_numpy(flux).cuda(), off, W)
+        torch.cuda.synchronize()
+        rt, rd = oracle.detrend_batch(flux, off, W)
+        compare_trend(tr.cpu().numpy(), rt, what="tiny curves")
+        compare_detr(de.cpu().numpy(), rd, what="tiny curves")
+    finally:
+        umi.clear_tuning()
+
+
 def test_plan_rule_choices(umi):
     """The planner's regimes on this GPU: single curves take a 32-lane
     variant where one covers W within 2W (every window can start a chain),
