@@ -815,7 +815,8 @@ def serving_leg(umi, torch, dev, args):
            "steady_state": "requests arriving after the first %.0f s" % SERVE_STEADY_AFTER_S,
            "rates": []}
     peak = 0
-    for rate, n in ((1000.0, min(R, 3000)), (5000.0, min(R, 10000)), (20000.0, R), (50000.0, R)):
+    for rate, n in ((1000.0, min(R, 3000)), (2000.0, min(R, 6000)), (5000.0, min(R, 10000)),
+                    (10000.0, min(R, 50000)), (20000.0, R), (50000.0, R)):
         with umi.Server(mem_budget_bytes=SERVE_BUDGET, n_streams=4, max_batch_curves=512) as srv:
             t = srv.submit(st.flux(0), int(W_req[0]))
             srv.wait(t, 60)
@@ -836,7 +837,7 @@ def serving_leg(umi, torch, dev, args):
                      "batches of at most 512 curves")
     out["peak_resident_bytes"] = peak
     out["serialized_rates"] = []
-    for rate, n in ((1000.0, min(R, 3000)), (20000.0, R)):
+    for rate, n in ((1000.0, min(R, 3000)), (10000.0, min(R, 50000)), (20000.0, R)):
         arr, lat, wall, offered = serialized_at_rate(umi, torch, st, tapes_pinned, W_req, rate, n, dev)
         out["serialized_rates"].append(latency_summary(arr, lat, wall, offered, rate, n))
     hi = [r for r in out["rates"] if r["rate_hz"] == 20000.0][0]
