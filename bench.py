@@ -46,8 +46,8 @@ LANES_PER_SM = 128
 # headline workload, from the ncu capture of that workload, valid only while
 # the kernel's code (comments and blank lines removed) hashes to
 # `kernel_sha256`.
-MEASURED_TRAFFIC = {"bytes": 162.56e6,
-                    "kernel_sha256": "edc71fe8871a4e0ef2db61c1899a6ad528431d2ff780337c5303920567a2e102"}
+MEASURED_TRAFFIC = {"bytes": 163.21e6,
+                    "kernel_sha256": "2a3fbde5e10130d5ec7a10f13b1d1e5d5daa3f4dca3238a1f28aeea1a73ad6e5"}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2604_06602_gb300", "csrc", "umi_kernel.cuh")
 
 
