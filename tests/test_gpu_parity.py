@@ -124,6 +124,18 @@ def test_parameter_presets(umi, preset):
                  what="alpha=%g c=%g" % preset)
 
 
+@pytest.mark.parametrize("c", [0.3, 1e4])
+@pytest.mark.parametrize("alpha", [2.0, 10.0])
+def test_extreme_tuning_constant(umi, c, alpha):
+    """c far from the paper's presets, in both sign-select forms: c = 0.3
+    leaves most samples outside the bisquare support (zero weight), c = 1e4
+    gives every sample a weight near 1 (a plain mean)."""
+    x = synth.config1().curve(0)[:5000].copy()
+    p = umi.params(alpha=alpha, c=c)
+    compare_diag(run_diag(umi, x, 361, p), oracle.detrend(x, 361, alpha=alpha, c=c), c=c,
+                 what="alpha=%g c=%g" % (alpha, c))
+
+
 @pytest.mark.parametrize("iters", [0, 1, 2, 7])
 def test_iteration_counts(umi, iters):
     x = synth.config1().curve(0)[:3000].copy()
