@@ -124,12 +124,12 @@ def test_parameter_presets(umi, preset):
                  what="alpha=%g c=%g" % preset)
 
 
-@pytest.mark.parametrize("c", [0.3, 1e4])
+@pytest.mark.parametrize("c", [0.02, 0.3, 1e4])
 @pytest.mark.parametrize("alpha", [2.0, 10.0])
 def test_extreme_tuning_constant(umi, c, alpha):
-    """c far from the paper's presets, in both sign-select forms: c = 0.3
-    leaves most samples outside the bisquare support (zero weight), c = 1e4
-    gives every sample a weight near 1 (a plain mean)."""
+    """c far from the paper's presets, in both sign-select forms: c = 0.02
+    and 0.3 leave most samples outside the bisquare support (zero weight),
+    c = 1e4 gives every sample a weight near 1 (a plain mean)."""
     x = synth.config1().curve(0)[:5000].copy()
     p = umi.params(alpha=alpha, c=c)
     compare_diag(run_diag(umi, x, 361, p), oracle.detrend(x, 361, alpha=alpha, c=c), c=c,
