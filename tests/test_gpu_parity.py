@@ -148,8 +148,10 @@ def test_zero_centred_and_scaled(umi):
     1e-5 of max(|trend|, c s) here."""
     rng = np.random.default_rng(77)
     # sigma 5e-20: the squared residuals of Eq. 1 are subnormal (about 2.5e-39),
-    # so the mean square takes the kernel's IEEE root instead of rsqrt.
-    for level, sigma in ((0.0, 1.0), (0.0, 1e-6), (1e4, 30.0), (-5.0, 0.1), (0.0, 5e-20)):
+    # so the mean square takes the kernel's IEEE root instead of rsqrt; level
+    # 1e15 and sigma 1e17 take mean squares near 1e26 and 1e34.
+    for level, sigma in ((0.0, 1.0), (0.0, 1e-6), (1e4, 30.0), (-5.0, 0.1), (0.0, 5e-20),
+                         (1e15, 1e13), (0.0, 1e17)):
         x = (level + sigma * rng.standard_normal(3000)).astype(np.float32)
         x[rng.uniform(size=x.size) < 0.03] = np.nan
         compare_diag(run_diag(umi, x, 129), oracle.detrend(x, 129), scale_aware=True,
