@@ -296,9 +296,8 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
     // This form serves 1/4 <= alpha <= 4, where u_eff^2 stays within
     // 4 + 1.5 (a^2 - 1) units of its value for the window's sigma (1.6e-6
     // relative at a = 4); every other alpha takes the min of two scaled
-    // residuals.  With r = 1/sqrt(msq) (Phase 2),
-    // sigma = r k1 in that form, and in the other kp = r k1, kn = alpha kp
-    // (k1 negated when alpha < 1).
+    // residuals.  With r = 1/sqrt(msq) (Phase 2), sigma = r k1 in that form,
+    // and in the other kp = r k1, kn = alpha kp (k1 negated when alpha < 1).
     const bool abs_form = alpha >= 0.25f && alpha <= 4.f;
     const float rho = fmaf(-alpha, alpha, 1.f) / fmaf(alpha, alpha, 1.f);
     const float k1 = (abs_form ? sqrtf(0.5f * fmaf(alpha, alpha, 1.f)) : (alpha >= 1.f ? 1.f : -1.f)) /
