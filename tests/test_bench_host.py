@@ -3,8 +3,10 @@ sampled oracle check the benchmark reports for every workload accepts the
 oracle's own outputs and rejects a planted error; steady-state latency
 percentiles drop the first second; the serving stream follows its mixture and
 every request's flux is a slice inside its class's tape; the kernel code hash
-that keys the measured traffic ignores comments."""
+that keys the measured traffic ignores comments; each band is tuned on its
+own curves."""
 import numpy as np
+import pytest
 
 import bench
 import oracle
@@ -81,3 +83,53 @@ def test_kernel_code_hash_ignores_comments_only(tmp_path, monkeypatch):
     assert bench.kernel_sha256() == h0
     src.write_text("// header\nint f(int x)\n{\n    return x + 2;  /* one */\n}\n")
     assert bench.kernel_sha256() != h0
+
+
+class _FakeTuner:
+    """Records the tuning calls tune_for_batch makes (no GPU)."""
+
+    def __init__(self, latency_below):
+        self.batch_calls, self.single_calls = [], []
+        self.latency_below = latency_below
+
+    def autotune_batch(self, W, lengths, flux=None):
+        self.batch_calls.append((W, np.asarray(lengths).copy(), flux.clone()))
+
+    def autotune(self, W, positions):
+        self.single_calls.append((W, positions))
+
+    def get_plan(self, W, positions):
+        return {"latency": int(positions < self.latency_below)}
+
+
+def test_tune_for_batch_tunes_each_band_on_its_own_curves():
+    """Each window length is tuned on its own curves: every k-th when the
+    band holds more than 2e7 positions, repeated up to 1e6 when it holds
+    fewer; the flux handed over is those curves back to back; a single
+    latency-regime median curve is tuned on its own."""
+    torch = pytest.importorskip("torch")
+    b = synth.config3(n_curves=40)
+    W = np.array([oracle.window_length(c) for c in b.cadence], np.int32)
+    flux = torch.from_numpy(b.flux)
+    fake = _FakeTuner(latency_below=20000)
+    bench.tune_for_batch(fake, b, W, flux)
+    assert [c[0] for c in fake.batch_calls] == sorted(set(W.tolist()))
+    for w, lens, got in fake.batch_calls:
+        idx = np.flatnonzero(W == w)
+        own = b.lengths[idx]
+        reps = lens.size // own.size
+        assert reps * own.size == lens.size and lens.sum() >= 1_000_000
+        assert np.array_equal(lens, np.tile(own, reps))
+        want = np.concatenate([b.curve(int(i)) for i in idx] * reps)
+        assert np.array_equal(got.numpy(), want, equal_nan=True)
+    meds = {w: int(np.median(b.lengths[W == w])) for w in set(W.tolist())}
+    assert fake.single_calls == [(w, meds[w]) for w in sorted(meds) if meds[w] < 20000]
+    # A band above 2e7 positions is sampled: every k-th curve.
+    big = synth.config2(n_curves=1200)
+    Wb = np.full(big.B, 361, np.int32)
+    fake = _FakeTuner(latency_below=0)
+    bench.tune_for_batch(fake, big, Wb, torch.from_numpy(big.flux))
+    (w, lens, got), = fake.batch_calls
+    assert lens.size == 600 and lens.sum() <= 20_000_000
+    assert np.array_equal(got[:18000].numpy(), big.curve(0), equal_nan=True)
+    assert np.array_equal(got[18000:36000].numpy(), big.curve(2), equal_nan=True)
