@@ -46,8 +46,8 @@ LANES_PER_SM = 128
 # headline workload, from the ncu capture of that workload, valid only while
 # the kernel's code (comments and blank lines removed) hashes to
 # `kernel_sha256`.
-MEASURED_TRAFFIC = {"bytes": 163.21e6,
-                    "kernel_sha256": "2a3fbde5e10130d5ec7a10f13b1d1e5d5daa3f4dca3238a1f28aeea1a73ad6e5"}
+MEASURED_TRAFFIC = {"bytes": 163.02e6,
+                    "kernel_sha256": "006aa279044fa5dccee93fc0fde15514b0bfb5f854327c42d3daa2726affd0c7"}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2604_06602_gb300", "csrc", "umi_kernel.cuh")
 
 

@@ -584,9 +584,19 @@ __device__ __forceinline__ void process_chain(const Curve &cv, const Diag &dg, c
                                 v = make_float2(fmaf(rho, fabsf(ts.x), ts.x), fmaf(rho, fabsf(ts.y), ts.y));
                             }
                             const float2 z = make_float2(fma_sat(-ts.x, v.x, 1.f), fma_sat(-ts.y, v.y, 1.f));
-                            const float2 w = __fmul2_rn(z, z);
-                            swt = __fadd2_rn(swt, w);
-                            swyt = __ffma2_rn(w, x[k], swyt);
+                            if constexpr (G == 1) {
+                                // sum z^2 and sum z (z y): the same three
+                                // packed instructions, scheduled 1.6 % faster
+                                // in the one-lane variants (the W = 25 band)
+                                // and 1 % slower in the others.
+                                const float2 zy = __fmul2_rn(z, x[k]);
+                                swt = __ffma2_rn(z, z, swt);
+                                swyt = __ffma2_rn(z, zy, swyt);
+                            } else {
+                                const float2 w = __fmul2_rn(z, z);
+                                swt = __fadd2_rn(swt, w);
+                                swyt = __ffma2_rn(w, x[k], swyt);
+                            }
                         }
                         const float sws = group_sum<G>(swt.x + swt.y);
                         const float swys = group_sum<G>(swyt.x + swyt.y);
